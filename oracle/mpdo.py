@@ -1,0 +1,219 @@
+"""The MPDO noisy-circuit simulator of Sec. II.C-II.D, FP64 NumPy.  Test infrastructure only.
+
+State: one rank-4 tensor per qubit, T[l, p, n, r] (left bond, physical, Kraus
+leg, right bond), Sec. II.C.  The represented density matrix is
+rho = sum_{n_0..n_{N-1}} |psi_n><psi_n| with psi_n[p_0..p_{N-1}] the matrix
+product T_0[:, p_0, n_0, :] ... T_{N-1}[:, p_{N-1}, n_{N-1}, :], which is the
+open-chain trace of the local densities M = sum_n T T* of Sec. II.C.
+
+Steps, in the paper's order:
+  * a noisy gate is K_i = N_i U (Eq. for K_i in Sec. II.C; noise after the gate);
+    its Kraus index becomes a new leg joined to the site's Kraus leg (Fig. 2b,c);
+    for a two-qubit gate the new leg joins the right site q+1;
+  * bond truncation (Fig. 3b): the chain is kept in canonical form by QR sweeps
+    and the two-site tensor is split by an SVD that keeps the top chi_max values;
+  * Kraus-leg truncation (Eq. svdNoise, Fig. 3a): the site tensor as a
+    (p, l, r) x n matrix is SVD-truncated to kappa_max values, T' = U S (= T V).
+Readings where the paper is silent: truncation runs per gate with the
+orthogonality centre on the touched sites; after a two-qubit gate the bond is
+split first and the right site's Kraus leg truncated second; nothing is
+renormalised and every readout is divided by Tr(rho); singular values at or
+below tol * sigma_max are dropped as numerically zero.
+
+Pinned by tests/test_oracle_mpdo.py against the dense simulator (no truncation,
+1e-12), the Eckart-Young identity of Sec. II.D and the exactness of the
+decomposition when the caps are at least the ranks.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .channels import chi_to_kraus
+
+
+class MPDO:
+    def __init__(self, n: int, chi_max: int, kappa_max: int, tol: float = 1e-13,
+                 auto_truncate: bool = True):
+        self.n = n
+        self.chi_max = chi_max
+        self.kappa_max = kappa_max
+        self.tol = tol
+        self.auto_truncate = auto_truncate
+        site = np.zeros((1, 2, 1, 1), dtype=np.complex128)
+        site[0, 0, 0, 0] = 1.0
+        self.sites = [site.copy() for _ in range(n)]
+        self.centre = 0
+        self.discarded_chi = 0.0
+        self.discarded_kappa = 0.0
+        self.min_gap = np.inf   # smallest (s_k^2 - s_{k+1}^2)/s_1^2 over truncations that cut
+        self.log = []           # (kind, site, kept, available, discarded weight)
+
+    # ------------------------------------------------------------ canonical form
+    def _shift_right(self, q: int) -> None:
+        A = self.sites[q]
+        dl, _, dn, dr = A.shape
+        Q, R = np.linalg.qr(A.reshape(dl * 2 * dn, dr))
+        self.sites[q] = Q.reshape(dl, 2, dn, Q.shape[1])
+        self.sites[q + 1] = np.einsum("xb,bpnr->xpnr", R, self.sites[q + 1])
+
+    def _shift_left(self, q: int) -> None:
+        A = self.sites[q]
+        dl, _, dn, dr = A.shape
+        Q, R = np.linalg.qr(A.reshape(dl, 2 * dn * dr).conj().T)  # A = R^dag Q^dag
+        self.sites[q] = Q.conj().T.reshape(Q.shape[1], 2, dn, dr)
+        self.sites[q - 1] = np.einsum("lpnb,bx->lpnx", self.sites[q - 1], R.conj().T)
+
+    def move_centre(self, q: int) -> None:
+        """QR sweeps that leave every site left of q left-isometric and right of q right-isometric."""
+        while self.centre < q:
+            self._shift_right(self.centre)
+            self.centre += 1
+        while self.centre > q:
+            self._shift_left(self.centre)
+            self.centre -= 1
+
+    # ------------------------------------------------------------ truncation
+    def _keep(self, s: np.ndarray, cap: int):
+        """How many singular values to keep, and the discarded weight sum_{dropped} s^2 / sum s^2."""
+        total = float(np.sum(s ** 2))
+        if total == 0.0:
+            return 1, 0.0
+        nz = int(np.sum(s > self.tol * s[0]))
+        k = max(1, min(cap, nz))
+        dropped = float(np.sum(s[k:] ** 2)) / total
+        if k < nz:
+            self.min_gap = min(self.min_gap, float((s[k - 1] ** 2 - s[k] ** 2) / s[0] ** 2))
+        return k, dropped
+
+    def truncate_kraus(self, q: int, kappa: int = 0) -> float:
+        """Eq. (svdNoise): T as a (p, l, r) x n matrix = U S V^dag; keep the top kappa; T' = T V."""
+        cap = kappa if kappa > 0 else self.kappa_max
+        self.move_centre(q)
+        A = self.sites[q]
+        dl, _, dn, dr = A.shape
+        M = A.transpose(0, 1, 3, 2).reshape(dl * 2 * dr, dn)
+        _, s, Vh = np.linalg.svd(M, full_matrices=False)
+        k, w = self._keep(s, cap)
+        Mt = M @ Vh[:k].conj().T
+        self.sites[q] = Mt.reshape(dl, 2, dr, k).transpose(0, 1, 3, 2).copy()
+        self.discarded_kappa += w
+        self.log.append(("kappa", q, k, len(s), w))
+        return w
+
+    # ------------------------------------------------------------ noisy gates
+    def apply_1q(self, q: int, U: np.ndarray, kraus) -> None:
+        """T'[l, p', (k, n), r] = sum_p (N_k U)[p', p] T[l, p, n, r]; then Kraus-leg truncation."""
+        self.move_centre(q)
+        K = np.stack([N @ U for N in kraus])  # [k, p', p]
+        A = self.sites[q]
+        dl, _, dn, dr = A.shape
+        At = np.einsum("kab,lbnr->laknr", K, A)              # new leg index k * dn + n
+        self.sites[q] = At.reshape(dl, 2, len(kraus) * dn, dr)
+        if self.auto_truncate:
+            self.truncate_kraus(q)
+
+    def apply_2q(self, q: int, U: np.ndarray, kraus) -> None:
+        """Two-site update on (q, q+1): merge, apply K_k = N_k U with a new Kraus leg on site q+1,
+        split by the SVD of the (l, p1, n1) x (p2, k, n2, r) matrix keeping chi_max values, then
+        truncate the Kraus leg of site q+1."""
+        self.move_centre(q)
+        A1, A2 = self.sites[q], self.sites[q + 1]
+        dl, _, dn1, _ = A1.shape
+        _, _, dn2, dr = A2.shape
+        rk = len(kraus)
+        K = np.stack([N @ U for N in kraus]).reshape(rk, 2, 2, 2, 2)  # [k, p1', p2', p1, p2]
+        theta = np.einsum("lanb,bcmr->lancmr", A1, A2)                # [l, p1, n1, p2, n2, r]
+        theta = np.einsum("kxyac,lancmr->lxnykmr", K, theta)          # [l, p1', n1, p2', k, n2, r]
+        mat = theta.reshape(dl * 2 * dn1, 2 * rk * dn2 * dr)
+        Um, s, Vh = np.linalg.svd(mat, full_matrices=False)
+        k, w = self._keep(s, self.chi_max)
+        self.sites[q] = Um[:, :k].reshape(dl, 2, dn1, k)
+        self.sites[q + 1] = (s[:k, None] * Vh[:k]).reshape(k, 2, rk * dn2, dr)
+        self.centre = q + 1
+        self.discarded_chi += w
+        self.log.append(("chi", q, k, len(s), w))
+        if self.auto_truncate:
+            self.truncate_kraus(q + 1)
+
+    # ------------------------------------------------------------ readouts
+    def _bra_ket(self, ops) -> complex:
+        """sum_n <psi_n| (x)_i O_i |psi_n>, O_i = ops.get(i, I); E'[r,r'] = sum E[l,l'] T*[l,p,n,r] O[p,p'] T[l',p',n,r']."""
+        E = np.ones((1, 1), dtype=np.complex128)
+        for i, A in enumerate(self.sites):
+            O = ops.get(i)
+            B = A if O is None else np.einsum("ab,lbnr->lanr", O, A)
+            E = np.einsum("xy,xpnr,ypns->rs", E, A.conj(), B)
+        return complex(E[0, 0])
+
+    def trace(self) -> float:
+        return self._bra_ket({}).real
+
+    def expect_product(self, ops) -> float:
+        return self._bra_ket(ops).real / self.trace()
+
+    def expect_zz(self, i: int, j: int) -> float:
+        Z = np.diag([1.0, -1.0]).astype(np.complex128)
+        return self.expect_product({i: Z, j: Z})
+
+    def zz_map(self) -> np.ndarray:
+        out = np.zeros((self.n, self.n))
+        for i in range(self.n):
+            out[i, i] = 1.0
+            for j in range(i + 1, self.n):
+                out[i, j] = out[j, i] = self.expect_zz(i, j)
+        return out
+
+    def element(self, a, b) -> complex:
+        """<a| rho |b> for computational basis strings a, b: E'[r,r'] = sum E[l,l'] T[l,a_i,n,r] T*[l',b_i,n,r']."""
+        E = np.ones((1, 1), dtype=np.complex128)
+        for i, A in enumerate(self.sites):
+            E = np.einsum("xy,xnr,yns->rs", E, A[:, a[i]], A[:, b[i]].conj())
+        return complex(E[0, 0])
+
+    def ghz_fidelity(self) -> float:
+        z, o = [0] * self.n, [1] * self.n
+        f = 0.5 * (self.element(z, z) + self.element(o, o) + 2 * self.element(z, o)).real
+        return f / self.trace()
+
+    def maxcut(self, edges) -> float:
+        return sum(0.5 * (1 - self.expect_zz(i, k)) for i, k in edges)
+
+    def purity(self) -> float:
+        """Tr(rho^2) / Tr(rho)^2 with rho_pq rho_qp contracted through a four-copy transfer."""
+        E = np.ones((1, 1, 1, 1), dtype=np.complex128)
+        for A in self.sites:
+            Ac = A.conj()
+            X = np.einsum("abcd,apnr->bcdpnr", E, A)        # copy 1, ket
+            X = np.einsum("bcdpnr,bqns->cdprqs", X, Ac)     # copy 1, bra (Kraus leg n summed)
+            X = np.einsum("cdprqs,cqmt->dprsmt", X, A)      # copy 2, ket
+            E = np.einsum("dprsmt,dpmu->rstu", X, Ac)       # copy 2, bra (Kraus leg m summed)
+        return E[0, 0, 0, 0].real / self.trace() ** 2
+
+    def dense(self) -> np.ndarray:
+        """rho = sum_n |psi_n><psi_n| as a 2^n x 2^n matrix (small n only), accumulated site by site
+        as R[P, P', r, r'] = sum R[P, P', l, l'] T[l, p, n, r] T*[l', p', n, r'] (Kraus legs summed)."""
+        R = np.ones((1, 1, 1, 1), dtype=np.complex128)
+        for A in self.sites:
+            R = np.einsum("abxy,xpnr->abypnr", R, A)
+            R = np.einsum("abypnr,yqns->apbqrs", R, A.conj())
+            s = R.shape
+            R = R.reshape(s[0] * 2, s[2] * 2, s[4], s[5])
+        return R[:, :, 0, 0]
+
+    def bond_dims(self):
+        return [A.shape[3] for A in self.sites[:-1]]
+
+    def kraus_dims(self):
+        return [A.shape[2] for A in self.sites]
+
+
+def run_circuit(circuit, chi_max: int, kappa_max: int, tol: float = 1e-13, kraus_tol: float = 1e-12) -> MPDO:
+    """Convert every channel from its chi matrix (Sec. III) and apply the ops in order."""
+    kraus = [chi_to_kraus(chi, nq, kraus_tol) for nq, chi in circuit.chis]
+    st = MPDO(circuit.n, chi_max, kappa_max, tol)
+    for op in circuit.ops:
+        if op.kind == 1:
+            st.apply_1q(op.q, op.U, kraus[op.chan])
+        else:
+            st.apply_2q(op.q, op.U, kraus[op.chan])
+    return st

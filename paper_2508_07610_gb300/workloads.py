@@ -1,0 +1,374 @@
+"""Seeded synthetic inputs for the noisy-circuit MPDO update.
+
+This module only prepares inputs: gate unitaries, standard noise channels as
+Kraus sets, their Pauli-basis process (chi) matrices, and circuits shaped like
+the workloads the simulator is run on.  None of the simulator's own arithmetic
+(chi -> Choi -> Kraus conversion, site contraction, truncation, readout) lives
+here.  Both the CPU reference and the CUDA library take these objects as inputs.
+
+Conventions (shared by every consumer):
+  * Pauli order I, X, Y, Z; a two-qubit Pauli index is m = 4*a + b with a on the
+    first (lower-numbered) qubit.
+  * Two-qubit matrices use the basis index 2*p_q + p_{q+1} (q is the MSB).
+  * A channel's chi matrix follows Eq. (chi) of Sec. III with unnormalised Pauli
+    strings, so a trace-preserving channel has Tr(chi) = 1.
+  * Rotations R_P(t) = exp(-i t P / 2); the QAOA mixer is exp(-i b X) and the
+    cost gate exp(-i g (1 - Z Z) / 2) as written in Sec. IV.B.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Sequence, Tuple
+
+import numpy as np
+
+I2 = np.eye(2, dtype=np.complex128)
+PX = np.array([[0, 1], [1, 0]], dtype=np.complex128)
+PY = np.array([[0, -1j], [1j, 0]], dtype=np.complex128)
+PZ = np.array([[1, 0], [0, -1]], dtype=np.complex128)
+PAULIS = (I2, PX, PY, PZ)
+
+MASTER_SEED = 0x2508076100
+
+
+# --------------------------------------------------------------------------
+# gates
+# --------------------------------------------------------------------------
+def rot(P: np.ndarray, theta: float) -> np.ndarray:
+    """exp(-i theta P / 2) for a Pauli-like P with P @ P = I."""
+    n = P.shape[0]
+    return math.cos(theta / 2) * np.eye(n, dtype=np.complex128) - 1j * math.sin(theta / 2) * P
+
+
+def rx(t):
+    return rot(PX, t)
+
+
+def ry(t):
+    return rot(PY, t)
+
+
+def rz(t):
+    return rot(PZ, t)
+
+
+def hadamard() -> np.ndarray:
+    return np.array([[1, 1], [1, -1]], dtype=np.complex128) / math.sqrt(2)
+
+
+def cz() -> np.ndarray:
+    return np.diag([1, 1, 1, -1]).astype(np.complex128)
+
+
+def swap() -> np.ndarray:
+    m = np.zeros((4, 4), dtype=np.complex128)
+    m[0, 0] = m[3, 3] = 1
+    m[1, 2] = m[2, 1] = 1
+    return m
+
+
+def zz_phase(phi: float) -> np.ndarray:
+    """exp(-i phi Z Z / 2): the coherent ZZ error of the two-qubit channels."""
+    zz = np.array([1, -1, -1, 1], dtype=np.float64)
+    return np.diag(np.exp(-0.5j * phi * zz))
+
+
+def qaoa_cost(gamma: float) -> np.ndarray:
+    """exp(-i gamma (1 - Z Z) / 2) on one edge (Sec. IV.B)."""
+    zz = np.array([1, -1, -1, 1], dtype=np.float64)
+    return np.diag(np.exp(-0.5j * gamma * (1.0 - zz)))
+
+
+def qaoa_mixer(beta: float) -> np.ndarray:
+    """exp(-i beta X) (Sec. IV.B)."""
+    return math.cos(beta) * I2 - 1j * math.sin(beta) * PX
+
+
+# --------------------------------------------------------------------------
+# channels as Kraus sets
+# --------------------------------------------------------------------------
+def depolarizing_1q(p: float) -> List[np.ndarray]:
+    """The printed single-qubit Kraus set of Sec. II.A: sqrt(1-3p/4) I, sqrt(p/4) X/Y/Z."""
+    return [math.sqrt(1 - 3 * p / 4) * I2] + [math.sqrt(p / 4) * P for P in (PX, PY, PZ)]
+
+
+def depolarizing_2q(p: float) -> List[np.ndarray]:
+    """(1-p) rho + p I/4: sqrt(1-15p/16) II and sqrt(p/16) for the 15 other Pauli pairs."""
+    out = []
+    for a in range(4):
+        for b in range(4):
+            w = 1 - 15 * p / 16 if (a == 0 and b == 0) else p / 16
+            out.append(math.sqrt(w) * np.kron(PAULIS[a], PAULIS[b]))
+    return out
+
+
+def amplitude_damping(g: float) -> List[np.ndarray]:
+    k0 = np.array([[1, 0], [0, math.sqrt(1 - g)]], dtype=np.complex128)
+    k1 = np.array([[0, math.sqrt(g)], [0, 0]], dtype=np.complex128)
+    return [k0, k1]
+
+
+def unitary_channel(U: np.ndarray) -> List[np.ndarray]:
+    return [np.asarray(U, dtype=np.complex128)]
+
+
+def compose(second: Sequence[np.ndarray], first: Sequence[np.ndarray]) -> List[np.ndarray]:
+    """Kraus set of `second` applied after `first`."""
+    return [B @ A for A in first for B in second]
+
+
+def pauli_strings(nq: int) -> List[np.ndarray]:
+    out = [np.ones((1, 1), dtype=np.complex128)]
+    for _ in range(nq):
+        out = [np.kron(o, P) for o in out for P in PAULIS]
+    return out
+
+
+def kraus_to_chi(kraus: Sequence[np.ndarray]) -> np.ndarray:
+    """Process matrix of a Kraus set in the unnormalised Pauli basis.
+
+    Writing K_k = sum_m c_km sigma_m (c_km = Tr(sigma_m K_k) / d) gives
+    eps(rho) = sum_mn (sum_k c_km conj(c_kn)) sigma_m rho sigma_n^dagger.
+    """
+    d = kraus[0].shape[0]
+    nq = int(round(math.log2(d)))
+    basis = pauli_strings(nq)
+    c = np.array([[np.trace(P.conj().T @ K) / d for P in basis] for K in kraus])
+    return c.T @ c.conj()
+
+
+# --------------------------------------------------------------------------
+# circuits
+# --------------------------------------------------------------------------
+@dataclasses.dataclass
+class Op:
+    """One noisy gate: `kind` is 1 or 2 (qubits q or q, q+1); U is the ideal gate,
+    `chan` indexes Circuit.chis (the channel applied after the gate)."""
+    kind: int
+    q: int
+    U: np.ndarray
+    chan: int
+
+
+@dataclasses.dataclass
+class Circuit:
+    n: int
+    ops: List[Op]
+    chis: List[Tuple[int, np.ndarray]]  # (nq, chi matrix): what the simulator is given
+    kraus: List[List[np.ndarray]] = dataclasses.field(default_factory=list)  # the sets chi was built from
+    meta: dict = dataclasses.field(default_factory=dict)
+
+    def n_2q(self) -> int:
+        return sum(1 for o in self.ops if o.kind == 2)
+
+
+class _Chans(list):
+    """chi matrices plus the Kraus sets they were synthesised from."""
+
+    def __init__(self):
+        super().__init__()
+        self.kraus = []
+
+
+def _add_chan(chis, nq, kraus) -> int:
+    chis.append((nq, kraus_to_chi(kraus)))
+    chis.kraus.append([np.asarray(K, dtype=np.complex128) for K in kraus])
+    return len(chis) - 1
+
+
+def _circuit(n, ops, chis, meta) -> "Circuit":
+    return Circuit(n, ops, list(chis), list(chis.kraus), meta)
+
+
+def ghz_ansatz(n: int = 6, depth: int = 3, seed: int = MASTER_SEED + 1) -> Circuit:
+    """Plain n-qubit GHZ-preparation ansatz: per layer Ry(theta) on every qubit then a CZ
+    ladder on (i, i+1).  Each 1q gate carries AD(2e-3) o DEP(1e-3) o Ry(eps), eps ~ N(0, 0.02);
+    each CZ carries DEP2(1e-2) o ZZ(phi), phi ~ N(0, 0.01)."""
+    rng = np.random.default_rng(seed)
+    ops, chis = [], _Chans()
+    for _ in range(depth):
+        for q in range(n):
+            th = rng.uniform(-math.pi, math.pi)
+            eps = rng.normal(0.0, 0.02)
+            k = compose(amplitude_damping(2e-3), compose(depolarizing_1q(1e-3), unitary_channel(ry(eps))))
+            ops.append(Op(1, q, ry(th), _add_chan(chis, 1, k)))
+        for q in range(n - 1):
+            phi = rng.normal(0.0, 0.01)
+            k = compose(depolarizing_2q(1e-2), unitary_channel(zz_phase(phi)))
+            ops.append(Op(2, q, cz(), _add_chan(chis, 2, k)))
+    return _circuit(n, ops, chis, {"name": f"ghz_ansatz_n{n}_d{depth}"})
+
+
+def hea_channels(n: int, rng) -> Tuple[list, list, list]:
+    """Per-qubit 1q channels AD(g) o DEP(p1) and per-pair 2q channels DEP2(p2) o ZZ(phi)."""
+    chis = _Chans()
+    c1 = []
+    for _ in range(n):
+        p1 = rng.uniform(5e-4, 2e-3)
+        g = rng.uniform(1e-3, 4e-3)
+        c1.append(_add_chan(chis, 1, compose(amplitude_damping(g), depolarizing_1q(p1))))
+    c2 = []
+    for _ in range(n - 1):
+        p2 = rng.uniform(5e-3, 2e-2)
+        phi = rng.normal(0.0, 0.01)
+        c2.append(_add_chan(chis, 2, compose(depolarizing_2q(p2), unitary_channel(zz_phase(phi)))))
+    return chis, c1, c2
+
+
+def hea_layer_ops(n: int, layer: int, rng, c1, c2) -> List[Op]:
+    """One hardware-efficient layer: Rz.Ry.Rz per qubit, then CZ on bonds of parity layer % 2."""
+    ops = []
+    for q in range(n):
+        a, b, c = rng.uniform(-math.pi, math.pi, size=3)
+        ops.append(Op(1, q, rz(c) @ ry(b) @ rz(a), c1[q]))
+    for q in range(layer % 2, n - 1, 2):
+        ops.append(Op(2, q, cz(), c2[q]))
+    return ops
+
+
+def hea(n: int = 20, depth: int = 10, seed: int = MASTER_SEED + 2) -> Circuit:
+    rng = np.random.default_rng(seed)
+    chis, c1, c2 = hea_channels(n, rng)
+    ops = []
+    for layer in range(depth):
+        ops += hea_layer_ops(n, layer, rng, c1, c2)
+    return _circuit(n, ops, chis, {"name": f"hea_n{n}_d{depth}"})
+
+
+def random_regular3(n: int, rng) -> List[Tuple[int, int]]:
+    """Uniform-ish random simple 3-regular graph by the configuration model with rejection."""
+    assert n % 2 == 0 and n >= 4
+    while True:
+        stubs = np.repeat(np.arange(n), 3)
+        rng.shuffle(stubs)
+        pairs = stubs.reshape(-1, 2)
+        edges = set()
+        ok = True
+        for a, b in pairs:
+            a, b = int(a), int(b)
+            if a == b or (min(a, b), max(a, b)) in edges:
+                ok = False
+                break
+            edges.add((min(a, b), max(a, b)))
+        if ok:
+            return sorted(edges)
+
+
+def qaoa_maxcut(n: int, p: int, edges, gammas, betas, rng, chis=None, c1=None, c2=None, cswap=None) -> Circuit:
+    """Noisy QAOA for MaxCut on a 1D chain: H layer, then per layer a full odd-even
+    transposition SWAP network (n rounds) in which every adjacent pair that is a graph edge
+    receives the cost gate fused with its SWAP, followed by the mixer on every qubit.
+    meta['perm'][i] is the logical vertex sitting at chain position i at the end."""
+    if chis is None:
+        chis, c1, c2 = hea_channels(n, rng)
+        cswap = []
+        for q in range(n - 1):
+            p2 = rng.uniform(5e-3, 2e-2)
+            phi = rng.normal(0.0, 0.01)
+            cswap.append(_add_chan(chis, 2, compose(depolarizing_2q(2 * p2), unitary_channel(zz_phase(phi)))))
+    eset = set((min(a, b), max(a, b)) for a, b in edges)
+    ops = [Op(1, q, hadamard(), c1[q]) for q in range(n)]
+    pos = list(range(n))  # pos[i] = logical vertex at chain position i
+    fused_cache = {}
+    for layer in range(p):
+        g, b = gammas[layer], betas[layer]
+        for rnd in range(n):
+            for q in range(rnd % 2, n - 1, 2):
+                u, v = pos[q], pos[q + 1]
+                if (min(u, v), max(u, v)) in eset:
+                    key = (layer, q)
+                    # cost gate with its 2q channel, then SWAP with the SWAP channel, as one update
+                    U = swap() @ qaoa_cost(g)
+                    ck = fused_cache.get(key)
+                    if ck is None:
+                        kc = chis.kraus[c2[q]]
+                        ks = chis.kraus[cswap[q]]
+                        sw = swap()
+                        moved = [sw @ K @ sw.conj().T for K in kc]
+                        ck = _add_chan(chis, 2, compose(ks, moved))
+                        fused_cache[key] = ck
+                    ops.append(Op(2, q, U, ck))
+                else:
+                    ops.append(Op(2, q, swap(), cswap[q]))
+                pos[q], pos[q + 1] = pos[q + 1], pos[q]
+        for q in range(n):
+            ops.append(Op(1, q, qaoa_mixer(b), c1[q]))
+    return _circuit(n, ops, chis, {"name": f"qaoa_n{n}_p{p}", "edges": sorted(eset), "perm": pos,
+                                   "gammas": list(gammas), "betas": list(betas)})
+
+
+def qaoa_batch(count: int, seed: int = MASTER_SEED + 3, n_choices=tuple(range(8, 25, 2)), p_max: int = 4):
+    """Batched noisy QAOA MaxCut instances: n ~ U{8,10,..,24} (3-regular graphs need even n),
+    p ~ U{1..4}, gamma_k, beta_k ~ U(0, pi)."""
+    ss = np.random.SeedSequence(seed)
+    out = []
+    for child in ss.spawn(count):
+        rng = np.random.default_rng(child)
+        n = int(rng.choice(n_choices))
+        p = int(rng.integers(1, p_max + 1))
+        edges = random_regular3(n, rng)
+        gam = rng.uniform(0, math.pi, size=p)
+        bet = rng.uniform(0, math.pi, size=p)
+        out.append(qaoa_maxcut(n, p, edges, gam, bet, rng))
+    return out
+
+
+def crosstalk_sweep(n: int = 40, depth: int = 20, seed: int = MASTER_SEED + 4) -> Circuit:
+    """Random 1D circuit with simultaneous CZ layers and crosstalk: per layer a random
+    R in {RX, RY, RZ} per qubit with angle U(0, 2 pi], CZ on bonds of parity layer % 2, then a
+    crosstalk channel (ZZ phase ~ N(0, 0.03) with DEP2(2e-3)) on every idle bond next to an
+    active pair, once per adjacent active pair.  A final 1q layer closes the circuit."""
+    rng = np.random.default_rng(seed)
+    chis, c1, c2 = hea_channels(n, rng)
+    ops = []
+    rots = (rx, ry, rz)
+
+    def one_q_layer():
+        for q in range(n):
+            r = rots[int(rng.integers(0, 3))]
+            t = 2 * math.pi - rng.uniform(0, 2 * math.pi)
+            ops.append(Op(1, q, r(t), c1[q]))
+
+    eye4 = np.eye(4, dtype=np.complex128)
+    for layer in range(depth):
+        one_q_layer()
+        active = list(range(layer % 2, n - 1, 2))
+        for q in active:
+            ops.append(Op(2, q, cz(), c2[q]))
+        for q in active:
+            for nb in (q - 1, q + 1):
+                if 0 <= nb < n - 1 and nb not in active:
+                    phi = rng.normal(0.0, 0.03)
+                    ck = _add_chan(chis, 2, compose(depolarizing_2q(2e-3), unitary_channel(zz_phase(phi))))
+                    ops.append(Op(2, nb, eye4, ck))
+    one_q_layer()
+    return _circuit(n, ops, chis, {"name": f"crosstalk_n{n}_d{depth}"})
+
+
+def random_unitary(d: int, rng) -> np.ndarray:
+    z = (rng.normal(size=(d, d)) + 1j * rng.normal(size=(d, d))) / math.sqrt(2)
+    q, r = np.linalg.qr(z)
+    return q * (np.diag(r) / np.abs(np.diag(r)))
+
+
+def random_channel_kraus(nq: int, rank: int, rng) -> List[np.ndarray]:
+    """A random CPTP map of the given Kraus rank (isometry columns split into Kraus blocks)."""
+    d = 2 ** nq
+    V = random_unitary(d * rank, rng)[:, :d]
+    return [V[k * d:(k + 1) * d, :] for k in range(rank)]
+
+
+def random_circuit(n: int, n_ops: int, rng, rank1: int = 3, rank2: int = 6, p2q: float = 0.5) -> Circuit:
+    """Unstructured random noisy circuit: random unitaries with random CPTP channels."""
+    ops, chis = [], _Chans()
+    for _ in range(n_ops):
+        if n > 1 and rng.uniform() < p2q:
+            q = int(rng.integers(0, n - 1))
+            ch = _add_chan(chis, 2, random_channel_kraus(2, rank2, rng))
+            ops.append(Op(2, q, random_unitary(4, rng), ch))
+        else:
+            q = int(rng.integers(0, n))
+            ch = _add_chan(chis, 1, random_channel_kraus(1, rank1, rng))
+            ops.append(Op(1, q, random_unitary(2, rng), ch))
+    return _circuit(n, ops, chis, {"name": f"random_n{n}_{n_ops}"})

@@ -1,0 +1,141 @@
+"""Pins for the CPU MPDO reference: exact agreement with the dense simulator when nothing is
+truncated, the Eckart-Young identity of Sec. II.D for every truncation, canonical-form
+invariants, and the readouts against their dense definitions."""
+import numpy as np
+import pytest
+
+from oracle import channels as C
+from oracle import dense as D
+from oracle import mpdo as M
+from paper_2508_07610_gb300 import workloads as W
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_no_truncation_matches_dense(seed):
+    rng = np.random.default_rng(seed)
+    n = 4
+    circ = W.random_circuit(n, 12, rng, rank1=3, rank2=5)
+    rho = D.run_circuit(circ)
+    st = M.run_circuit(circ, chi_max=64, kappa_max=4096)
+    assert st.discarded_chi < 1e-24 and st.discarded_kappa < 1e-24
+    assert np.max(np.abs(st.dense() - rho)) < 1e-12
+    assert abs(st.trace() - 1) < 1e-12
+    for i in range(n):
+        for j in range(i + 1, n):
+            assert abs(st.expect_zz(i, j) - D.expect_zz(rho, n, i, j)) < 1e-12
+    assert abs(st.ghz_fidelity() - D.ghz_fidelity(rho, n)) < 1e-12
+    assert abs(st.purity() - D.purity(rho)) < 1e-12
+
+
+def test_ghz_ansatz_small_no_truncation():
+    circ = W.ghz_ansatz(n=4, depth=2)
+    rho = D.run_circuit(circ)
+    st = M.run_circuit(circ, chi_max=64, kappa_max=4096)
+    assert np.max(np.abs(st.dense() - rho)) < 1e-12
+    assert abs(st.ghz_fidelity() - D.ghz_fidelity(rho, 4)) < 1e-12
+
+
+def test_eckart_young_kraus_truncation():
+    rng = np.random.default_rng(11)
+    st = M.MPDO(3, 16, 3)
+    st.auto_truncate = False
+    circ = W.random_circuit(3, 8, rng, rank1=4, rank2=8)
+    kr = [C.chi_to_kraus(chi, nq) for nq, chi in circ.chis]
+    for op in circ.ops:
+        (st.apply_1q if op.kind == 1 else st.apply_2q)(op.q, op.U, kr[op.chan])
+    q = 1
+    st.move_centre(q)
+    A = st.sites[q].copy()
+    full = np.sum(np.abs(A) ** 2)
+    w = st.truncate_kraus(q, kappa=2)
+    B = st.sites[q]
+    # ||T - T'||_F^2 / ||T||_F^2 with T' = T V V^dag, computed from the kept tensor T V
+    dl, _, dn, dr = A.shape
+    Tm = A.transpose(0, 1, 3, 2).reshape(-1, dn)
+    Bm = B.transpose(0, 1, 3, 2).reshape(-1, B.shape[2])
+    V = np.linalg.lstsq(Tm, Bm, rcond=None)[0]
+    err = np.sum(np.abs(Tm - Bm @ V.conj().T) ** 2) / full
+    assert w > 1e-6
+    assert abs(err - w) < 1e-12
+    # and it is the best rank-2 approximation: no other rank-2 projector does better
+    for _ in range(20):
+        Z = np.linalg.qr(rng.normal(size=(dn, 2)) + 1j * rng.normal(size=(dn, 2)))[0]
+        assert np.sum(np.abs(Tm - Tm @ Z @ Z.conj().T) ** 2) / full >= w - 1e-12
+
+
+def test_bond_truncation_weight_matches_state_error():
+    # With the centre on the pair, the discarded bond weight equals the squared distance between
+    # the purified states before and after the split (Eckart-Young on the two-site matrix).
+    rng = np.random.default_rng(5)
+    n = 4
+    circ = W.random_circuit(n, 10, rng, rank1=2, rank2=4)
+    kr = [C.chi_to_kraus(chi, nq) for nq, chi in circ.chis]
+    big = M.MPDO(n, 64, 4096)
+    small = M.MPDO(n, 64, 4096)
+    for op in circ.ops:
+        for st in (big, small):
+            (st.apply_1q if op.kind == 1 else st.apply_2q)(op.q, op.U, kr[op.chan])
+    small.chi_max = 3
+    U = W.random_unitary(4, rng)
+    kr2 = W.random_channel_kraus(2, 3, rng)
+    big.auto_truncate = small.auto_truncate = False
+    big.apply_2q(1, U, kr2)
+    small.apply_2q(1, U, kr2)
+    w = small.log[-1][4]
+    assert w > 1e-8
+    # the kept part is orthogonal to the dropped part, so Tr rho_small = (1 - w) Tr rho_big
+    assert abs(small.trace() - (1 - w) * big.trace()) < 1e-12
+
+
+def test_canonical_form_after_moves():
+    rng = np.random.default_rng(8)
+    circ = W.random_circuit(5, 14, rng)
+    st = M.run_circuit(circ, 8, 4)
+    for c in (0, 4, 2):
+        st.move_centre(c)
+        for q in range(c):
+            A = st.sites[q]
+            m = A.reshape(-1, A.shape[3])
+            assert np.allclose(m.conj().T @ m, np.eye(m.shape[1]), atol=1e-12)
+        for q in range(c + 1, 5):
+            A = st.sites[q]
+            m = A.reshape(A.shape[0], -1)
+            assert np.allclose(m @ m.conj().T, np.eye(m.shape[0]), atol=1e-12)
+        # with the centre at c, Tr rho is the squared norm of the centre tensor
+        assert abs(st.trace() - np.sum(np.abs(st.sites[c]) ** 2)) < 1e-12
+
+
+def test_truncated_state_is_valid_density_matrix():
+    circ = W.ghz_ansatz(n=6, depth=3)
+    st = M.run_circuit(circ, 4, 2)
+    rho = st.dense()
+    rho = rho / np.trace(rho)
+    assert np.max(np.abs(rho - rho.conj().T)) < 1e-13
+    assert np.linalg.eigvalsh(rho).min() > -1e-13
+    assert st.discarded_chi > 0 and st.discarded_kappa > 0
+
+
+def test_readouts_against_dense_under_truncation():
+    circ = W.ghz_ansatz(n=6, depth=3)
+    st = M.run_circuit(circ, 6, 3)
+    rho = st.dense()
+    assert abs(st.ghz_fidelity() - D.ghz_fidelity(rho, 6)) < 1e-12
+    assert abs(st.purity() - D.purity(rho)) < 1e-12
+    edges = [(0, 1), (1, 2), (2, 5), (0, 4)]
+    assert abs(st.maxcut(edges) - D.maxcut_expectation(rho, 6, edges)) < 1e-12
+    zz = st.zz_map()
+    for i in range(6):
+        for j in range(6):
+            if i != j:
+                assert abs(zz[i, j] - D.expect_zz(rho, 6, i, j)) < 1e-12
+
+
+def test_truncation_converges_with_caps():
+    circ = W.ghz_ansatz(n=4, depth=2)
+    rho = D.run_circuit(circ)
+    f_exact = D.ghz_fidelity(rho, 4)
+    errs = []
+    for chi, kap in [(2, 1), (4, 2), (8, 4), (64, 4096)]:
+        errs.append(abs(M.run_circuit(circ, chi, kap).ghz_fidelity() - f_exact))
+    assert errs[-1] < 1e-12
+    assert errs[0] > errs[-1]
