@@ -1,0 +1,399 @@
+// Batched Hermitian eigensolver for the truncation steps: the top-k eigenpairs of an n x n
+// Hermitian matrix, one CTA per matrix (CUDA cores, FP32 or FP64).
+//
+// The SVD truncations of Sec. II.D (Eq. svdNoise for the Kraus leg, Fig. 3b for the bond) only
+// need the leading singular subspace of a tall or wide matrix X, i.e. the top eigenpairs of its
+// Gram matrix X X^H; this kernel supplies them.  The Choi-matrix eigendecomposition of Sec. III
+// (chi -> Kraus) uses it with k = n in FP64.
+//
+// Steps: (1) Householder reduction to a complex Hermitian tridiagonal (matrix kept in global
+// memory, which the L2 holds), followed by a diagonal phase change that makes it real symmetric;
+// (2) bisection with Sturm counts for the top k eigenvalues, one thread per eigenvalue;
+// (3) inverse iteration on the tridiagonal (LU with partial pivoting) from distinct
+// pseudo-random starts, one thread per vector; (4) classical Gram-Schmidt applied twice, in
+// descending eigenvalue order, which also separates vectors of (near-)degenerate eigenvalues;
+// (5) back-transformation through the phases and the Householder reflectors, one warp per vector.
+// Every loop is bounded; the input matrix is overwritten.
+#include "kernels.h"
+
+namespace mpdo {
+
+namespace {
+constexpr int NT = 256;
+constexpr int MAXN = 512;
+
+template <typename R>
+__device__ R block_sum(R v, R* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  R s = 0;
+  for (int w = 0; w < NT / 32; ++w) s += red[w];
+  return s;
+}
+
+template <typename R>
+__device__ cplx<R> block_csum(cplx<R> v, R* red) {
+  R a = block_sum(v.x, red);
+  R b = block_sum(v.y, red);
+  return mk(a, b);
+}
+
+__device__ __forceinline__ uint32_t hash32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+
+template <typename R>
+__device__ __forceinline__ R eps_of();
+template <>
+__device__ __forceinline__ float eps_of<float>() { return 1.1920929e-07f; }
+template <>
+__device__ __forceinline__ double eps_of<double>() { return 2.220446049250313e-16; }
+
+// number of eigenvalues of the real symmetric tridiagonal (d, e2 = e^2) below sigma
+template <typename R>
+__device__ int sturm_count(const R* d, const R* e2, int n, R sigma, R pivmin) {
+  int cnt = 0;
+  R q = d[0] - sigma;
+  if (fabs(q) < pivmin) q = -pivmin;
+  if (q < R(0)) ++cnt;
+  for (int i = 1; i < n; ++i) {
+    q = d[i] - sigma - e2[i - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    if (q < R(0)) ++cnt;
+  }
+  return cnt;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(NT) heevk_kernel(EigArgs<R> g) {
+  __shared__ R red[NT / 32];
+  __shared__ R s_d[MAXN], s_e2[MAXN], s_beta[MAXN];
+  __shared__ cplx<R> s_p[MAXN], s_v[MAXN];
+  __shared__ R s_w[MAXN];
+  __shared__ cplx<R> s_v0[MAXN];
+  __shared__ int s_flag;
+  const int z = blockIdx.x;
+  const int n = g.n, k = g.k;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  cplx<R>* A = g.A + (int64_t)z * g.astride;
+  R* S = g.scratch + (int64_t)z * g.sstride;
+  // scratch layout (R units, vector t element i at [i * k + t] so threads walk it coalesced)
+  R* Ldl = S;
+  R* Ldd = Ldl + (int64_t)n * k;
+  R* Ldu = Ldd + (int64_t)n * k;
+  R* Ldu2 = Ldu + (int64_t)n * k;
+  R* Lpiv = Ldu2 + (int64_t)n * k;
+  R* Zr = Lpiv + (int64_t)n * k;
+  cplx<R>* U = reinterpret_cast<cplx<R>*>(Zr + (int64_t)n * k);   // complex, vector t column at [t * n]
+  cplx<R>* PH = U + (int64_t)n * k;                                  // phases, n
+
+  // ---- (1) tridiagonalisation: A <- H A H on the trailing block, H = I - beta v v^H
+  for (int j = 0; j + 2 < n; ++j) {
+    cplx<R>* col = A + (int64_t)j * n;
+    R s = 0;
+    for (int i = j + 2 + tid; i < n; i += NT) s += norm2(col[i]);
+    s = block_sum(s, red);
+    const cplx<R> a = col[j + 1];
+    const R aa = sqrt(norm2(a));
+    const R nrm = sqrt(aa * aa + s);
+    const cplx<R> ph = (aa > R(0)) ? mk<R>(a.x / aa, a.y / aa) : mk<R>(1, 0);
+    const R beta = (nrm > R(0)) ? R(1) / (nrm * (nrm + aa)) : R(0);
+    const cplx<R> v0 = a + nrm * ph;
+    for (int i = j + 1 + tid; i < n; i += NT) s_v[i] = (i == j + 1) ? v0 : col[i];
+    if (tid == 0) s_beta[j] = beta;
+    __syncthreads();
+    if (beta != R(0)) {
+      // p = beta * A_sub v
+      for (int i = j + 1 + tid; i < n; i += NT) {
+        cplx<R> acc = mk<R>(0, 0);
+        for (int c = j + 1; c < n; ++c) cfma(acc, A[(int64_t)c * n + i], s_v[c]);
+        s_p[i] = beta * acc;
+      }
+      __syncthreads();
+      // K = (beta / 2) v^H p ; w = p - K v
+      cplx<R> part = mk<R>(0, 0);
+      for (int i = j + 1 + tid; i < n; i += NT) cfma_cj(part, s_v[i], s_p[i]);
+      cplx<R> K = block_csum(part, red);
+      K = (beta * R(0.5)) * K;
+      for (int i = j + 1 + tid; i < n; i += NT) s_p[i] = s_p[i] - K * s_v[i];
+      __syncthreads();
+      // A_sub -= v w^H + w v^H
+      for (int64_t e = tid; e < (int64_t)(n - j - 1) * (n - j - 1); e += NT) {
+        int i = j + 1 + (int)(e % (n - j - 1)), c = j + 1 + (int)(e / (n - j - 1));
+        cplx<R> t = A[(int64_t)c * n + i];
+        t = t - s_v[i] * conjg(s_p[c]) - s_p[i] * conjg(s_v[c]);
+        A[(int64_t)c * n + i] = t;
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      col[j + 1] = (nrm > R(0)) ? mk<R>(-nrm * ph.x, -nrm * ph.y) : a;  // the new subdiagonal e_j
+      s_v0[j] = v0;  // v_{j+1}; v_i for i >= j + 2 stay in col[i]
+    }
+    __syncthreads();
+  }
+  // diagonal, |off-diagonal|^2 and the phases Phi that make the tridiagonal real:
+  // T_real = Phi^H T Phi with phi_0 = 1, phi_{j+1} = phi_j e_j / |e_j|
+  for (int i = tid; i < n; i += NT) s_d[i] = A[(int64_t)i * n + i].x;
+  if (tid == 0) {
+    cplx<R> phi = mk<R>(1, 0);
+    PH[0] = phi;
+    for (int j = 0; j + 1 < n; ++j) {
+      cplx<R> e = A[(int64_t)j * n + j + 1];
+      R ae = sqrt(norm2(e));
+      s_e2[j] = ae * ae;
+      if (ae > R(0)) phi = phi * mk<R>(e.x / ae, e.y / ae);
+      PH[j + 1] = phi;
+    }
+  }
+  __syncthreads();
+
+  // ---- (2) bisection for the top kk = min(k + 1, n) eigenvalues (descending)
+  const int kk = (k < n) ? k + 1 : n;
+  R gl = s_d[0], gu = s_d[0], emax2 = 0, trace = 0;
+  for (int i = 0; i < n; ++i) {
+    R r = 0;
+    if (i > 0) r += sqrt(s_e2[i - 1]);
+    if (i + 1 < n) r += sqrt(s_e2[i]);
+    gl = fmin(gl, s_d[i] - r);
+    gu = fmax(gu, s_d[i] + r);
+    if (i + 1 < n) emax2 = fmax(emax2, s_e2[i]);
+    trace += s_d[i];
+  }
+  const R eps = eps_of<R>();
+  const R tnorm = fmax(fabs(gl), fabs(gu));
+  const R pivmin = R(1e-30) * fmax(R(1), emax2);
+  const R abstol = eps * tnorm + pivmin;
+  gl -= R(2) * eps * tnorm * n + pivmin;
+  gu += R(2) * eps * tnorm * n + pivmin;
+  for (int t = tid; t < kk; t += NT) {
+    const int target = n - 1 - t;  // ascending index of the t-th largest eigenvalue
+    R lo = gl, hi = gu;
+    for (int it = 0; it < 256; ++it) {
+      R mid = R(0.5) * (lo + hi);
+      if (hi - lo <= R(2) * eps * fmax(fabs(lo), fabs(hi)) + abstol || mid == lo || mid == hi) break;
+      if (sturm_count(s_d, s_e2, n, mid, pivmin) > target) hi = mid; else lo = mid;
+    }
+    s_w[t] = R(0.5) * (lo + hi);
+  }
+  __syncthreads();
+
+  // ---- (3) inverse iteration, one thread per vector t < k
+  const R pert = eps * fmax(tnorm, R(1e-30));
+  for (int t = tid; t < k; t += NT) {
+    const R lam = s_w[t];
+    // LU with partial pivoting of T - lam I (diagonals dd, du, du2; multipliers dl; pivots)
+    for (int i = 0; i < n; ++i) {
+      Ldd[(int64_t)i * k + t] = s_d[i] - lam;
+      if (i + 1 < n) {
+        R b = sqrt(s_e2[i]);
+        Ldu[(int64_t)i * k + t] = b;
+        Ldl[(int64_t)i * k + t] = b;
+      }
+      Ldu2[(int64_t)i * k + t] = 0;
+      Lpiv[(int64_t)i * k + t] = 0;
+    }
+    for (int i = 0; i + 1 < n; ++i) {
+      R di = Ldd[(int64_t)i * k + t], li = Ldl[(int64_t)i * k + t];
+      if (fabs(di) >= fabs(li)) {
+        if (di == R(0)) { di = pert; Ldd[(int64_t)i * k + t] = di; }
+        R f = li / di;
+        Ldl[(int64_t)i * k + t] = f;
+        Ldd[(int64_t)(i + 1) * k + t] -= f * Ldu[(int64_t)i * k + t];
+      } else {
+        R f = di / li;
+        Ldd[(int64_t)i * k + t] = li;
+        Ldl[(int64_t)i * k + t] = f;
+        R tmp = Ldu[(int64_t)i * k + t];
+        R dnext = Ldd[(int64_t)(i + 1) * k + t];
+        Ldu[(int64_t)i * k + t] = dnext;
+        Ldd[(int64_t)(i + 1) * k + t] = tmp - f * dnext;
+        if (i + 2 < n) {
+          R unext = Ldu[(int64_t)(i + 1) * k + t];
+          Ldu2[(int64_t)i * k + t] = unext;
+          Ldu[(int64_t)(i + 1) * k + t] = -f * unext;
+        }
+        Lpiv[(int64_t)i * k + t] = 1;
+      }
+    }
+    if (Ldd[(int64_t)(n - 1) * k + t] == R(0)) Ldd[(int64_t)(n - 1) * k + t] = pert;
+    // start vector
+    for (int i = 0; i < n; ++i) {
+      uint32_t h = hash32((uint32_t)(t * 7919 + 1) * 2654435761u ^ (uint32_t)(i * 40503 + 17));
+      Zr[(int64_t)i * k + t] = R((int)(h >> 8) - (1 << 23)) / R(1 << 23);
+    }
+    for (int it = 0; it < 3; ++it) {
+      // forward: apply L^-1 with the row interchanges
+      for (int i = 0; i + 1 < n; ++i) {
+        R zi = Zr[(int64_t)i * k + t], zn = Zr[(int64_t)(i + 1) * k + t], f = Ldl[(int64_t)i * k + t];
+        if (Lpiv[(int64_t)i * k + t] != R(0)) {
+          Zr[(int64_t)i * k + t] = zn;
+          Zr[(int64_t)(i + 1) * k + t] = zi - f * zn;
+        } else {
+          Zr[(int64_t)(i + 1) * k + t] = zn - f * zi;
+        }
+      }
+      // backward: U z = y
+      R zmax = 0;
+      for (int i = n - 1; i >= 0; --i) {
+        R v = Zr[(int64_t)i * k + t];
+        if (i + 1 < n) v -= Ldu[(int64_t)i * k + t] * Zr[(int64_t)(i + 1) * k + t];
+        if (i + 2 < n) v -= Ldu2[(int64_t)i * k + t] * Zr[(int64_t)(i + 2) * k + t];
+        v /= Ldd[(int64_t)i * k + t];
+        if (!(fabs(v) < R(1e30))) v = (v > 0) ? R(1e30) : R(-1e30);
+        Zr[(int64_t)i * k + t] = v;
+        zmax = fmax(zmax, fabs(v));
+      }
+      R sc = (zmax > R(0)) ? R(1) / zmax : R(1);
+      R nn = 0;
+      for (int i = 0; i < n; ++i) {
+        R v = Zr[(int64_t)i * k + t] * sc;
+        Zr[(int64_t)i * k + t] = v;
+        nn += v * v;
+      }
+      R inv = (nn > R(0)) ? R(1) / sqrt(nn) : R(0);
+      for (int i = 0; i < n; ++i) Zr[(int64_t)i * k + t] *= inv;
+    }
+  }
+  __syncthreads();
+
+  // ---- (4) Gram-Schmidt (twice) in descending order; redo a vector that collapses
+  for (int t = 0; t < k; ++t) {
+    for (int attempt = 0; attempt < 3; ++attempt) {
+      for (int pass = 0; pass < 2; ++pass) {
+        // dots with all previous vectors: warp w handles previous vectors u = w, w + 8, ...
+        for (int u = wid; u < t; u += NT / 32) {
+          R acc = 0;
+          for (int i = lane; i < n; i += 32) acc += Zr[(int64_t)i * k + u] * Zr[(int64_t)i * k + t];
+          for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+          if (lane == 0) s_w[MAXN - 1 - u] = acc;  // dots parked at the tail of s_w (k + 1 <= MAXN / 2)
+        }
+        __syncthreads();
+        for (int i = tid; i < n; i += NT) {
+          R v = Zr[(int64_t)i * k + t];
+          for (int u = 0; u < t; ++u) v -= s_w[MAXN - 1 - u] * Zr[(int64_t)i * k + u];
+          Zr[(int64_t)i * k + t] = v;
+        }
+        __syncthreads();
+      }
+      R nn = 0;
+      for (int i = tid; i < n; i += NT) nn += Zr[(int64_t)i * k + t] * Zr[(int64_t)i * k + t];
+      nn = block_sum(nn, red);
+      if (tid == 0) s_flag = (nn > R(0.01)) ? 1 : 0;
+      __syncthreads();
+      const R inv = (nn > R(0)) ? R(1) / sqrt(nn) : R(0);
+      for (int i = tid; i < n; i += NT) Zr[(int64_t)i * k + t] *= inv;
+      __syncthreads();
+      if (s_flag || attempt == 2) break;
+      // collapsed: one more inverse-iteration step from a fresh start, then orthogonalise again
+      if (tid == 0) {
+        for (int i = 0; i < n; ++i) {
+          uint32_t h = hash32((uint32_t)(t * 104729 + attempt * 7 + 3) ^ (uint32_t)(i * 92821 + 5));
+          Zr[(int64_t)i * k + t] = R((int)(h >> 8) - (1 << 23)) / R(1 << 23);
+        }
+        for (int i = 0; i + 1 < n; ++i) {
+          R zi = Zr[(int64_t)i * k + t], zn = Zr[(int64_t)(i + 1) * k + t], f = Ldl[(int64_t)i * k + t];
+          if (Lpiv[(int64_t)i * k + t] != R(0)) {
+            Zr[(int64_t)i * k + t] = zn;
+            Zr[(int64_t)(i + 1) * k + t] = zi - f * zn;
+          } else {
+            Zr[(int64_t)(i + 1) * k + t] = zn - f * zi;
+          }
+        }
+        R zmax = 0;
+        for (int i = n - 1; i >= 0; --i) {
+          R v = Zr[(int64_t)i * k + t];
+          if (i + 1 < n) v -= Ldu[(int64_t)i * k + t] * Zr[(int64_t)(i + 1) * k + t];
+          if (i + 2 < n) v -= Ldu2[(int64_t)i * k + t] * Zr[(int64_t)(i + 2) * k + t];
+          v /= Ldd[(int64_t)i * k + t];
+          if (!(fabs(v) < R(1e30))) v = (v > 0) ? R(1e30) : R(-1e30);
+          Zr[(int64_t)i * k + t] = v;
+          zmax = fmax(zmax, fabs(v));
+        }
+        R sc = (zmax > R(0)) ? R(1) / zmax : R(1);
+        for (int i = 0; i < n; ++i) Zr[(int64_t)i * k + t] *= sc;
+      }
+      __syncthreads();
+    }
+  }
+
+  // ---- (5) back-transformation u = H_0 ... H_{n-3} Phi z, one warp per vector
+  for (int t = wid; t < k; t += NT / 32) {
+    cplx<R>* u = U + (int64_t)t * n;
+    for (int i = lane; i < n; i += 32) u[i] = Zr[(int64_t)i * k + t] * PH[i];
+    __syncwarp();
+    for (int j = n - 3; j >= 0; --j) {
+      const R beta = s_beta[j];
+      if (beta == R(0)) continue;
+      const cplx<R>* col = A + (int64_t)j * n;  // v_i = col[i] for i >= j + 2, v_{j+1} = s_v0[j]
+      cplx<R> acc = mk<R>(0, 0);
+      for (int i = j + 1 + lane; i < n; i += 32) {
+        cplx<R> vi = (i == j + 1) ? s_v0[j] : col[i];
+        cfma_cj(acc, vi, u[i]);
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+      }
+      acc = beta * acc;
+      for (int i = j + 1 + lane; i < n; i += 32) {
+        cplx<R> vi = (i == j + 1) ? s_v0[j] : col[i];
+        u[i] = u[i] - vi * acc;
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+
+  // ---- outputs
+  cplx<R>* V = g.V + view_batch(g.vv, z);
+  for (int64_t e = tid; e < (int64_t)n * k; e += NT) {
+    int i = (int)(e % n), t = (int)(e / n);
+    cplx<R> v = U[(int64_t)t * n + i];
+    if (g.vv.conj) v.y = -v.y;
+    V[view_row(g.vv, i) + view_col(g.vv, t)] = v;
+  }
+  if (g.w) {
+    R* w = g.w + (int64_t)z * g.wstride;
+    for (int t = tid; t < k; t += NT) w[t] = s_w[t];
+  }
+  if (tid == 0) {
+    double kept = 0;
+    for (int t = 0; t < k; ++t) kept += (double)s_w[t];
+    double tr = (double)trace;
+    if (g.disc && tr > 0) {
+      double w = (tr - kept) / tr;
+      if (w < 0) w = 0;
+      g.disc[(int64_t)z * g.disc_stride] += w;
+    }
+    if (g.gap && k < n && s_w[0] > R(0)) {
+      double gp = ((double)s_w[k - 1] - (double)s_w[k]) / (double)s_w[0];
+      double* gz = g.gap + (int64_t)z * g.disc_stride;
+      if (gp < *gz) *gz = gp;
+    }
+  }
+}
+}  // namespace
+
+int64_t eig_scratch_elems(int n, int k) { return 8 * (int64_t)n * k + 2 * (int64_t)n + 64; }
+
+template <typename R>
+cudaError_t heevk(cudaStream_t s, int batch, const EigArgs<R>& g) {
+  if (batch <= 0 || g.n <= 0 || g.k <= 0) return cudaSuccess;
+  if (g.n > MAXN || g.k > g.n || g.k + 1 > MAXN / 2) return cudaErrorInvalidValue;
+  heevk_kernel<R><<<batch, NT, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
+template cudaError_t heevk<float>(cudaStream_t, int, const EigArgs<float>&);
+template cudaError_t heevk<double>(cudaStream_t, int, const EigArgs<double>&);
+
+}  // namespace mpdo

@@ -1,0 +1,1352 @@
+// Host engine behind the C ABI: owns the device state of a batch of MPDO chains and sequences the
+// sm_103a kernels for each call.  Shapes are decided on the host from the gate sequence alone, so
+// no call reads device data to size its work and whole circuits can be captured in a CUDA graph.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <type_traits>
+#include <vector>
+
+#include "kernels.h"
+#include "mpdo.h"
+
+using namespace mpdo;
+
+struct mpdo_chanset {
+  int nq = 0, count = 0, rpad = 0;
+  int device = 0;
+  cplx<double>* kraus = nullptr;  // [count][rpad][d][d]
+  std::vector<int> ranks;
+  ~mpdo_chanset() {
+    if (kraus) cudaFree(kraus);
+  }
+};
+
+struct mpdo_graph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t stream = nullptr;
+  ~mpdo_graph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+  }
+};
+
+#define CK(x)                                                        \
+  do {                                                               \
+    cudaError_t e_ = (x);                                            \
+    if (e_ != cudaSuccess) {                                         \
+      last_err = e_;                                                 \
+      return e_ == cudaErrorInvalidValue ? MPDO_EINVAL : MPDO_ECUDA; \
+    }                                                                \
+  } while (0)
+
+namespace {
+
+inline int imin(int a, int b) { return a < b ? a : b; }
+inline int64_t lmax(int64_t a, int64_t b) { return a > b ? a : b; }
+
+View v2(int64_t bstride, int32_t rdiv, int64_t rhi, int64_t rlo, int32_t cdiv, int64_t chi, int64_t clo, int conj = 0) {
+  View v{};
+  v.blo = bstride;
+  v.rdiv = rdiv;
+  v.rhi = rhi;
+  v.rlo = rlo;
+  v.cdiv = cdiv;
+  v.chi = chi;
+  v.clo = clo;
+  v.conj = conj;
+  return v;
+}
+
+struct EngBase {
+  int B = 1, n = 0, chi_max = 1, kappa_max = 1, prec = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  bool capturing = false;
+  long long launches = 0;
+  cudaError_t last_err = cudaSuccess;
+  std::vector<int> bond;   // n + 1 entries, bond[0] = bond[n] = 1
+  std::vector<int> kraus;  // n entries
+  int centre = 0;
+  // capture snapshot
+  std::vector<int> snap_bond, snap_kraus, snap_slot;
+  int snap_centre = 0;
+
+  virtual ~EngBase() {}
+  virtual mpdo_status alloc() = 0;
+  virtual mpdo_status reset() = 0;
+  virtual mpdo_status apply(int nq, int q, const double* Uhost, const double* Udev, const mpdo_chanset* ch,
+                            const int* idx_dev) = 0;
+  virtual mpdo_status truncate(int q, int kappa, double* disc) = 0;
+  virtual mpdo_status expect(int kind, const int* args, int nargs, double* out) = 0;
+  virtual mpdo_status restore_layout() = 0;
+  virtual std::vector<int> slots() const = 0;
+  virtual mpdo_status save(FILE* f) = 0;
+  virtual mpdo_status get_site(int chain, int q, double* out) = 0;
+  virtual mpdo_status set_site(int q, int dl, int dn, int dr, const double* data) = 0;
+  virtual mpdo_status load(FILE* f) = 0;
+
+  mpdo_status sync() {
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+      last_err = e;
+      return MPDO_ECUDA;
+    }
+    return MPDO_OK;
+  }
+};
+
+template <typename R, typename ER>
+struct Eng : EngBase {
+  using C = cplx<R>;
+  using CE = cplx<ER>;
+  static constexpr int RMAX = 16;
+
+  // storage
+  C* pool = nullptr;
+  int nslots = 0;
+  int64_t slot_elems = 0;
+  std::vector<int> site_slot, free_slots;
+  // per-instance workspaces (each strided by its own size)
+  C *wQR = nullptr, *wQ = nullptr, *wE = nullptr, *wT = nullptr, *wZ = nullptr, *wF = nullptr, *wU = nullptr,
+    *wH = nullptr, *wY = nullptr, *wX = nullptr, *wK = nullptr, *wRt = nullptr;
+  int64_t sQR = 0, sE = 0, sT = 0, sZ = 0, sF = 0, sU = 0, sH = 0, sY = 0, sX = 0;
+  CE *wF64 = nullptr, *wU64 = nullptr;
+  ER *wEval = nullptr, *wScr = nullptr;
+  int64_t sEval = 0, sScr = 0;
+  double* dDisc = nullptr;  // [B][3]: chi, kappa, gap
+  // readout buffers
+  C *envL = nullptr, *envR = nullptr, *tmpA = nullptr, *tmpB = nullptr;
+  int64_t sEnv = 0, sTmp = 0;
+  cplx<double>* dDot = nullptr;
+  // purity buffers (lazy)
+  C *pX = nullptr, *pP = nullptr, *pE = nullptr, *pE2 = nullptr;
+  int64_t pCap = 0, pECap = 0;
+
+  ~Eng() override {
+    void* ptrs[] = {pool, wQR, wQ, wE, wT, wZ, wF, wU, wH, wY, wX, wK, wRt, wF64, wU64, wEval, wScr, dDisc,
+                    envL, envR, tmpA, tmpB, dDot, pX, pP, pE, pE2, iota};
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+  }
+
+  template <typename T>
+  cudaError_t dmalloc(T** p, int64_t count) {
+    return cudaMalloc((void**)p, sizeof(T) * (size_t)lmax(count, 1));
+  }
+
+  C* site_ptr(int q) const { return pool + (int64_t)site_slot[q] * B * slot_elems; }
+  C* slot_ptr(int s) const { return pool + (int64_t)s * B * slot_elems; }
+  int take_slot() {
+    int s = free_slots.back();
+    free_slots.pop_back();
+    return s;
+  }
+  void give_slot(int s) { free_slots.push_back(s); }
+
+  mpdo_status alloc() override {
+    const int64_t X = chi_max, K = kappa_max;
+    slot_elems = 2 * K * X * X;
+    nslots = n + 3;
+    CK(dmalloc(&pool, (int64_t)nslots * B * slot_elems));
+    sQR = 2 * K * X * X;
+    CK(dmalloc(&wQR, sQR * B));
+    CK(dmalloc(&wQ, sQR * B));
+    sE = 4 * X * X;
+    CK(dmalloc(&wE, sE * B));
+    sT = 16 * X * X;
+    CK(dmalloc(&wT, sT * B));
+    sZ = 16 * X * X;
+    CK(dmalloc(&wZ, sZ * B));
+    sF = lmax(16 * X * X, 256 * K * K);
+    CK(dmalloc(&wF, sF * B));
+    sU = lmax(4 * X * X, 16 * K * K);
+    CK(dmalloc(&wU, sU * B));
+    sH = 4 * X * X;
+    CK(dmalloc(&wH, sH * B));
+    sY = 4 * X * X * RMAX;
+    CK(dmalloc(&wY, sY * B));
+    sX = 2 * RMAX * K * X * X;
+    CK(dmalloc(&wX, sX * B));
+    CK(dmalloc(&wK, (int64_t)RMAX * 16 * B));
+    CK(dmalloc(&wRt, (int64_t)64 * B));
+    if (!std::is_same<R, ER>::value) {
+      CK(dmalloc(&wF64, sF * B));
+      CK(dmalloc(&wU64, sU * B));
+    }
+    sEval = lmax(4 * X, 16 * K) + 1;
+    CK(dmalloc(&wEval, sEval * B));
+    sScr = lmax(eig_scratch_elems((int)(4 * X), (int)X), eig_scratch_elems((int)(16 * K), (int)K));
+    sScr = lmax(sScr, eig_scratch_elems(16, 16));
+    CK(dmalloc(&wScr, sScr * B));
+    CK(dmalloc(&dDisc, (int64_t)3 * B));
+    sEnv = X * X;
+    CK(dmalloc(&envL, sEnv * B * (n + 1)));
+    CK(dmalloc(&envR, sEnv * B * (n + 1)));
+    sTmp = 2 * K * X * X;
+    CK(dmalloc(&tmpA, sTmp * B));
+    CK(dmalloc(&tmpB, sTmp * B));
+    CK(dmalloc(&dDot, (int64_t)B));
+    {
+      std::vector<int> h(B);
+      for (int b = 0; b < B; ++b) h[b] = b;
+      CK(dmalloc(&iota, (int64_t)B));
+      CK(cudaMemcpy(iota, h.data(), sizeof(int) * B, cudaMemcpyHostToDevice));
+    }
+    mpdo_status st = reset();
+    if (st) return st;
+    return sync();
+  }
+
+  mpdo_status reset() override {
+    bond.assign(n + 1, 1);
+    kraus.assign(n, 1);
+    centre = 0;
+    site_slot.resize(n);
+    free_slots.clear();
+    for (int q = 0; q < n; ++q) site_slot[q] = q;
+    for (int s = nslots - 1; s >= n; --s) free_slots.push_back(s);
+    // |0> product state: slot q of every chain holds [1, 0]
+    CK(init_zero_sites<R>(stream, n * B, pool, slot_elems));
+    CK(init_discarded(stream, B, dDisc));
+    launches += 2;
+    return MPDO_OK;
+  }
+
+  std::vector<int> slots() const override { return site_slot; }
+
+  // ---------------------------------------------------------------- kernels wrappers
+  mpdo_status gemm_(int M, int N, int K, const C* A, View va, const C* Bm, View vb, C* Cm, View vc, int batch = -1) {
+    GemmArgs<R> g;
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.alpha = mk<R>(1, 0);
+    g.beta = mk<R>(0, 0);
+    g.A = A;
+    g.va = va;
+    g.B = Bm;
+    g.vb = vb;
+    g.C = Cm;
+    g.vc = vc;
+    CK(gemm<R>(stream, batch < 0 ? B : batch, g));
+    ++launches;
+    return MPDO_OK;
+  }
+
+  // top-k eigenpairs of the column-major Hermitian matrices in wF (n x n), vectors to wU (col-major n x k)
+  mpdo_status eig_(int nmat, int k, int which /*0 chi, 1 kappa, -1 none*/) {
+    if (std::is_same<R, ER>::value) {
+      EigArgs<ER> a;
+      a.A = reinterpret_cast<CE*>(wF);
+      a.astride = sF;
+      a.n = nmat;
+      a.k = k;
+      a.w = wEval;
+      a.wstride = sEval;
+      a.V = reinterpret_cast<CE*>(wU);
+      a.vv = col_major(nmat, sU);
+      a.scratch = wScr;
+      a.sstride = sScr;
+      a.disc = which >= 0 ? dDisc + which : nullptr;
+      a.gap = which >= 0 ? dDisc + 2 : nullptr;
+      a.disc_stride = 3;
+      CK(heevk<ER>(stream, B, a));
+      ++launches;
+    } else {
+      // FP64 eigensolver on complex64 Gram matrices
+      CK((convert<R, ER>(stream, sF * B, wF, wF64)));
+      EigArgs<ER> a;
+      a.A = wF64;
+      a.astride = sF;
+      a.n = nmat;
+      a.k = k;
+      a.w = wEval;
+      a.wstride = sEval;
+      a.V = wU64;
+      a.vv = col_major(nmat, sU);
+      a.scratch = wScr;
+      a.sstride = sScr;
+      a.disc = which >= 0 ? dDisc + which : nullptr;
+      a.gap = which >= 0 ? dDisc + 2 : nullptr;
+      a.disc_stride = 3;
+      CK(heevk<ER>(stream, B, a));
+      CK((convert<ER, R>(stream, sU * B, wU64, wU)));
+      launches += 3;
+    }
+    return MPDO_OK;
+  }
+
+  // ---------------------------------------------------------------- canonical form
+  // centre c -> c + 1: QR of site c as ((l, p, n), r)
+  mpdo_status shift_right(int c) {
+    const int dl = bond[c], dn = kraus[c], dr = bond[c + 1];
+    const int m = dl * 2 * dn, x = imin(m, dr);
+    const int dn2 = kraus[c + 1], dr2 = bond[c + 2];
+    const int sa = take_slot(), sb = take_slot();
+    QrArgs<R> a;
+    a.m = m;
+    a.n = dr;
+    a.in = site_ptr(c);
+    a.vin = row_major(dr, slot_elems);
+    a.W = wQR;
+    a.wstride = sQR;
+    a.Qw = wQ;
+    a.qstride = sQR;
+    a.qout = slot_ptr(sa);
+    a.vq = row_major(x, slot_elems);
+    CK(qr<R>(stream, B, a));
+    ++launches;
+    // site c+1 <- R . A_{c+1}
+    const int N = 2 * dn2 * dr2;
+    mpdo_status st = gemm_(x, N, dr, wQR, col_major(m, sQR), site_ptr(c + 1), row_major(N, slot_elems),
+                           slot_ptr(sb), row_major(N, slot_elems));
+    if (st) return st;
+    give_slot(site_slot[c]);
+    give_slot(site_slot[c + 1]);
+    site_slot[c] = sa;
+    site_slot[c + 1] = sb;
+    bond[c + 1] = x;
+    return MPDO_OK;
+  }
+  // centre c -> c - 1: LQ of site c as (l, (p, n, r)) via QR of its conjugate transpose
+  mpdo_status shift_left(int c) {
+    const int dl = bond[c], dn = kraus[c], dr = bond[c + 1];
+    const int L = 2 * dn * dr, x = imin(L, dl);
+    const int dlp = bond[c - 1], dnp = kraus[c - 1];
+    const int sa = take_slot(), sb = take_slot();
+    QrArgs<R> a;
+    a.m = L;
+    a.n = dl;
+    a.in = site_ptr(c);
+    a.vin = v2(slot_elems, 0, 0, 1, 0, 0, L, 1);  // (i, j) -> conj(A[j * L + i])
+    a.W = wQR;
+    a.wstride = sQR;
+    a.Qw = wQ;
+    a.qstride = sQR;
+    a.qout = slot_ptr(sa);
+    a.vq = v2(slot_elems, 0, 0, 1, 0, 0, L, 1);  // Q^H written as the new x x L site
+    CK(qr<R>(stream, B, a));
+    ++launches;
+    // site c-1 <- A_{c-1} . R^H
+    const int M = dlp * 2 * dnp;
+    mpdo_status st = gemm_(M, x, dl, site_ptr(c - 1), row_major(dl, slot_elems), wQR, v2(sQR, 0, 0, L, 0, 0, 1, 1),
+                           slot_ptr(sb), row_major(x, slot_elems));
+    if (st) return st;
+    give_slot(site_slot[c]);
+    give_slot(site_slot[c - 1]);
+    site_slot[c] = sa;
+    site_slot[c - 1] = sb;
+    bond[c] = x;
+    return MPDO_OK;
+  }
+  mpdo_status move_centre(int q) {
+    while (centre < q) {
+      mpdo_status s = shift_right(centre);
+      if (s) return s;
+      ++centre;
+    }
+    while (centre > q) {
+      mpdo_status s = shift_left(centre);
+      if (s) return s;
+      --centre;
+    }
+    return MPDO_OK;
+  }
+
+  // ---------------------------------------------------------------- gate fusion
+  mpdo_status fuse_(int nq, const double* Uhost, const double* Udev, const mpdo_chanset* ch, const int* idx_dev) {
+    FuseArgs<R> f;
+    std::memset(&f, 0, sizeof(f));
+    f.nq = nq;
+    f.rk = ch->rpad;
+    const int d = 1 << nq;
+    if (Uhost)
+      for (int i = 0; i < d * d; ++i) f.U[i] = mk<double>(Uhost[2 * i], Uhost[2 * i + 1]);
+    f.Udev = reinterpret_cast<const cplx<double>*>(Udev);
+    f.kraus = ch->kraus;
+    f.chan_stride = (int64_t)ch->rpad * d * d;
+    f.chan_idx = idx_dev;
+    f.Khat = wK;
+    f.Rt = nq == 2 ? wRt : nullptr;
+    // idx_dev == nullptr: one channel for all, or channel b for chain b (handled by chan_idx below)
+    CK(fuse_gate<R>(stream, B, f));
+    ++launches;
+    return MPDO_OK;
+  }
+
+  // Kraus-leg truncation of a tensor held Kraus-major in wX: X[nk][s][r] (NK x S*dr) -> new site
+  // [l][p][nu][r] with S = dl*2 rows (l, p).  Eq. (svdNoise) through the Gram matrix X^* X^T.
+  mpdo_status kappa_truncate_X(int NK, int S, int dr, int kap, int out_slot) {
+    const int64_t L = (int64_t)S * dr;
+    // G = conj(X) X^T  (NK x NK, column-major)
+    mpdo_status st = gemm_(NK, NK, (int)L, wX, v2(sX, 0, 0, L, 0, 0, 1, 1), wX, v2(sX, 0, 0, 1, 0, 0, L, 0), wF,
+                           col_major(NK, sF));
+    if (st) return st;
+    st = eig_(NK, kap, 1);
+    if (st) return st;
+    // A[(s, nu, r)] = sum_nk V[nk, nu] X[nk][s][r]
+    return gemm_(kap, (int)L, NK, wU, v2(sU, 0, 0, NK, 0, 0, 1), wX, row_major(L, sX), slot_ptr(out_slot),
+                 v2(slot_elems, 0, 0, dr, dr, (int64_t)kap * dr, 1));
+  }
+
+  // ---------------------------------------------------------------- noisy gates
+  mpdo_status apply(int nq, int q, const double* Uhost, const double* Udev, const mpdo_chanset* ch,
+                    const int* idx_dev) override {
+    if (q < 0 || q + nq > n) return MPDO_EINVAL;
+    if (!ch || ch->nq != nq || ch->rpad > RMAX) return MPDO_EINVAL;
+    if (!idx_dev && ch->count != 1 && ch->count != B) return MPDO_EINVAL;
+    mpdo_status st = move_centre(q);
+    if (st) return st;
+    // with one channel per chain and no index array, chain b uses channel b
+    const int* idx = idx_dev;
+    if (!idx && ch->count == B && B > 1) idx = iota;
+    st = fuse_(nq, Uhost, Udev, ch, idx);
+    if (st) return st;
+    return nq == 1 ? apply1(q, ch->rpad) : apply2(q, ch->rpad);
+  }
+  int* iota = nullptr;  // device [0, 1, ..., B-1]
+
+  mpdo_status apply1(int q, int rk) {
+    const int dl = bond[q], dn = kraus[q], dr = bond[q + 1];
+    const int NK = rk * dn, S = 2 * dl;
+    CK(apply_1q_kraus<R>(stream, B, dl, dn, dr, rk, site_ptr(q), slot_elems, wK, wX, sX));
+    ++launches;
+    const int kap = imin(kappa_max, imin(S * dr, NK));
+    const int so = take_slot();
+    mpdo_status st = kappa_truncate_X(NK, S, dr, kap, so);
+    if (st) return st;
+    give_slot(site_slot[q]);
+    site_slot[q] = so;
+    kraus[q] = kap;
+    return MPDO_OK;
+  }
+
+  mpdo_status apply2(int q, int rk) {
+    const int dl = bond[q], dm = bond[q + 1], dr = bond[q + 2];
+    const int dn1 = kraus[q], dn2 = kraus[q + 1];
+    const int C2 = 2 * dm;
+    // 1. QR of A1 as ((l, n1), (p1, b)) -> Q1 (m x x, wQ), R1 (x x 2dm, wQR), column-major ld m
+    const int m = dl * dn1, x = imin(m, C2);
+    QrArgs<R> qa;
+    qa.m = m;
+    qa.n = C2;
+    qa.in = site_ptr(q);
+    qa.vin = v2(slot_elems, dn1, (int64_t)2 * dn1 * dm, dm, dm, (int64_t)dn1 * dm, 1);
+    qa.W = wQR;
+    qa.wstride = sQR;
+    qa.Qw = wQ;
+    qa.qstride = sQR;
+    qa.qout = nullptr;
+    CK(qr<R>(stream, B, qa));
+    ++launches;
+    const View R1 = col_major(m, sQR);
+    // 2. E = A2 A2^H with A2 as (2dm) x (dn2 dr)
+    const int K2 = dn2 * dr;
+    mpdo_status st = gemm_(C2, C2, K2, site_ptr(q + 1), row_major(K2, slot_elems), site_ptr(q + 1),
+                           v2(slot_elems, 0, 0, 1, 0, 0, K2, 1), wE, row_major(C2, sE));
+    if (st) return st;
+    // 3. T[c][a][c'][b] from E and the reduced superoperator of the fused gate
+    CK(build_T<R>(stream, B, dm, wRt, wE, sE, wT, sT));
+    ++launches;
+    // 4. Z[x][(a, c', b)] = sum_c R1[x, c] T[c][(a, c', b)]
+    const int NZ = 4 * C2;
+    st = gemm_(x, NZ, C2, wQR, R1, wT, row_major(NZ, sT), wZ, row_major(NZ, sZ));
+    if (st) return st;
+    // 5. F'[(x, a), (x', b)] = sum_c' Z[(x, a), (c', b)] conj(R1[x', c']); batch index = b * B + chain
+    {
+      const int X2 = 2 * x;
+      View va = v2(0, 0, 0, 2 * C2, 0, 0, 2);
+      va.bdiv = B;
+      va.bhi = 1;
+      va.blo = sZ;
+      View vb = v2(0, 0, 0, m, 0, 0, 1, 1);
+      vb.bdiv = B;
+      vb.bhi = 0;
+      vb.blo = sQR;
+      View vc = v2(0, 0, 0, 1, 0, 0, (int64_t)2 * X2);
+      vc.bdiv = B;
+      vc.bhi = X2;
+      vc.blo = sF;
+      st = gemm_(X2, x, C2, wZ, va, wQR, vb, wF, vc, 2 * B);
+      if (st) return st;
+    }
+    // 6. bond: top kchi eigenpairs of F'
+    const int kchi = imin(chi_max, imin(2 * x, 2 * dn2 * rk * dr));
+    st = eig_(2 * x, kchi, 0);
+    if (st) return st;
+    // 7. A1' [l][p1'][n1][b'] = sum_x Q1[(l, n1), x] U[(x, p1'), b']
+    const int s1 = take_slot();
+    st = gemm_(m, 2 * kchi, x, wQ, col_major(m, sQR), wU, v2(sU, 0, 0, 2, kchi, 1, (int64_t)2 * x),
+               slot_ptr(s1), v2(slot_elems, dn1, (int64_t)2 * dn1 * kchi, kchi, kchi, (int64_t)dn1 * kchi, 1));
+    if (st) return st;
+    // 8. H[(b', p1')][(p1, bb)] = sum_x conj(U[(x, p1'), b']) R1[x, (p1, bb)]
+    st = gemm_(2 * kchi, C2, x, wU, v2(sU, 2, (int64_t)2 * x, 1, 0, 0, 2, 1), wQR, R1, wH, row_major(C2, sH));
+    if (st) return st;
+    // 9. Y[(b', p2', k)][(bb, p2)] = sum Khat_k[(p1' p2'), (p1 p2)] H[(b', p1')][(p1, bb)]
+    CK(build_Y<R>(stream, B, kchi, dm, rk, wK, wH, sH, wY, sY));
+    ++launches;
+    // 10. X (Kraus-major [(k, n2)][(b', p2')][r]) = Y . A2
+    const int S = 2 * kchi, NK = rk * dn2;
+    const int64_t Lx = (int64_t)S * dr;
+    st = gemm_(S * rk, K2, C2, wY, row_major(C2, sY), site_ptr(q + 1), row_major(K2, slot_elems), wX,
+               v2(sX, rk, dr, (int64_t)dn2 * Lx, dr, Lx, 1));
+    if (st) return st;
+    // 11-13. Kraus-leg truncation of site q+1
+    const int kap = imin(kappa_max, imin((int)Lx, NK));
+    const int s2 = take_slot();
+    st = kappa_truncate_X(NK, S, dr, kap, s2);
+    if (st) return st;
+    give_slot(site_slot[q]);
+    give_slot(site_slot[q + 1]);
+    site_slot[q] = s1;
+    site_slot[q + 1] = s2;
+    bond[q + 1] = kchi;
+    kraus[q + 1] = kap;
+    centre = q + 1;
+    return MPDO_OK;
+  }
+
+  mpdo_status truncate(int q, int kappa, double* disc) override {
+    if (q < 0 || q >= n) return MPDO_EINVAL;
+    mpdo_status st = move_centre(q);
+    if (st) return st;
+    const int dl = bond[q], dn = kraus[q], dr = bond[q + 1];
+    int kap = kappa > 0 ? kappa : kappa_max;
+    kap = imin(kap, imin(dn, 2 * dl * dr));
+    std::vector<double> before;
+    if (disc) {
+      before.resize(3 * (size_t)B);
+      CK(cudaMemcpyAsync(before.data(), dDisc, sizeof(double) * 3 * B, cudaMemcpyDeviceToHost, stream));
+    }
+    // site [l][p][n][r] -> Kraus-major X[n][(l, p)][r]
+    const int S = 2 * dl;
+    CK(copy_view<R>(stream, B, dn, S * dr, site_ptr(q), v2(slot_elems, 0, 0, dr, dr, (int64_t)dn * dr, 1), wX,
+                    row_major((int64_t)S * dr, sX)));
+    ++launches;
+    const int so = take_slot();
+    st = kappa_truncate_X(dn, S, dr, kap, so);
+    if (st) return st;
+    give_slot(site_slot[q]);
+    site_slot[q] = so;
+    kraus[q] = kap;
+    if (disc) {
+      std::vector<double> after(3 * (size_t)B);
+      CK(cudaMemcpyAsync(after.data(), dDisc, sizeof(double) * 3 * B, cudaMemcpyDeviceToHost, stream));
+      CK(cudaStreamSynchronize(stream));
+      for (int b = 0; b < B; ++b) disc[b] = after[3 * b + 1] - before[3 * b + 1];
+    }
+    return MPDO_OK;
+  }
+
+  // ---------------------------------------------------------------- readouts
+  C* envl(int q) { return envL + (int64_t)q * B * sEnv; }
+  C* envr(int q) { return envR + (int64_t)q * B * sEnv; }
+
+  // E' = transfer of E (dl x dl) through site q, Z on the physical index when z
+  mpdo_status left_step(int q, const C* E, C* out, bool z) {
+    const int dl = bond[q], dn = kraus[q], dr = bond[q + 1];
+    const int N = 2 * dn * dr;
+    // tmp[l'][(p, n, r)] = sum_l E[l, l'] conj(A[l, (p, n, r)])
+    mpdo_status st = gemm_(dl, N, dl, E, v2(sEnv, 0, 0, 1, 0, 0, dl), site_ptr(q), v2(slot_elems, 0, 0, N, 0, 0, 1, 1),
+                           tmpA, row_major(N, sTmp));
+    if (st) return st;
+    if (z) {
+      CK(scale_odd<R>(stream, B, (int64_t)dl * N, (int64_t)dn * dr, R(-1), tmpA, sTmp));
+      ++launches;
+    }
+    // out[r, r'] = sum_{(l', p, n)} tmp[(l', p, n), r] A[(l', p, n), r']
+    return gemm_(dr, dr, dl * 2 * dn, tmpA, v2(sTmp, 0, 0, 1, 0, 0, dr), site_ptr(q), row_major(dr, slot_elems), out,
+                 row_major(dr, sEnv));
+  }
+  // E = right transfer of Rr (dr x dr) through site q
+  mpdo_status right_step(int q, const C* Rr, C* out, bool z) {
+    const int dl = bond[q], dn = kraus[q], dr = bond[q + 1];
+    const int M = dl * 2 * dn;
+    mpdo_status st = gemm_(M, dr, dr, site_ptr(q), row_major(dr, slot_elems), Rr, v2(sEnv, 0, 0, 1, 0, 0, dr), tmpA,
+                           row_major(dr, sTmp));
+    if (st) return st;
+    if (z) {
+      CK(scale_odd<R>(stream, B, (int64_t)M * dr, (int64_t)dn * dr, R(-1), tmpA, sTmp));
+      ++launches;
+    }
+    const int K = 2 * dn * dr;
+    return gemm_(dl, dl, K, site_ptr(q), v2(slot_elems, 0, 0, K, 0, 0, 1, 1), tmpA, v2(sTmp, 0, 0, 1, 0, 0, K), out,
+                 row_major(dl, sEnv));
+  }
+  mpdo_status one_env(C* E) {
+    cplx<R> one = mk<R>(1, 0);
+    for (int b = 0; b < B; ++b) {
+      CK(fill<R>(stream, 1, E + (int64_t)b * sEnv, one));
+      ++launches;
+    }
+    return MPDO_OK;
+  }
+  // sum_{r r'} E[r, r'] Rr[r, r'] per chain (Rr Hermitian: = sum conj(Rr^T) E, done as a dot of E with Rr^T*)
+  mpdo_status close_(const C* E, const C* Rr, int d, std::vector<double>& re) {
+    // tmpB = conj(Rr), so that dot(tmpB, E) = sum E[r, r'] Rr[r, r']
+    CK(copy_view<R>(stream, B, d, d, Rr, v2(sEnv, 0, 0, d, 0, 0, 1, 1), tmpB, row_major(d, sTmp)));
+    ++launches;
+    CK(dot_batch<R>(stream, B, (int64_t)d * d, tmpB, sTmp, E, sEnv, dDot));
+    ++launches;
+    std::vector<cplx<double>> h(B);
+    CK(cudaMemcpyAsync(h.data(), dDot, sizeof(cplx<double>) * B, cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    re.resize(B);
+    for (int b = 0; b < B; ++b) re[b] = h[b].x;
+    return MPDO_OK;
+  }
+  mpdo_status build_envs() {
+    mpdo_status st = one_env(envl(0));
+    if (st) return st;
+    for (int q = 0; q < n; ++q)
+      if ((st = left_step(q, envl(q), envl(q + 1), false))) return st;
+    if ((st = one_env(envr(n)))) return st;
+    for (int q = n - 1; q >= 0; --q)
+      if ((st = right_step(q, envr(q + 1), envr(q), false))) return st;
+    return MPDO_OK;
+  }
+  mpdo_status trace_(std::vector<double>& tr) { return close_(envl(n), envr(n), 1, tr); }
+
+  mpdo_status zz_pairs(const std::vector<std::pair<int, int>>& pairs, std::vector<std::vector<double>>& vals) {
+    vals.assign(pairs.size(), std::vector<double>(B, 0));
+    // group by i
+    for (int i = 0; i < n; ++i) {
+      int jmax = -1;
+      for (auto& p : pairs)
+        if (p.first == i) jmax = p.second > jmax ? p.second : jmax;
+      if (jmax < 0) continue;
+      // ping-pong E through tmp env slots: use envL storage of a scratch index n? use two buffers in wE/wT
+      C* Ea = wE;  // sE = 4 X^2 >= X^2
+      C* Eb = wT;
+      mpdo_status st = left_step_to(i, envl(i), Ea, true);
+      if (st) return st;
+      for (int j = i + 1; j <= jmax; ++j) {
+        // value with Z at j
+        if ((st = left_step_to(j, Ea, Eb, true))) return st;
+        bool need = false;
+        for (auto& p : pairs) need |= (p.first == i && p.second == j);
+        if (need) {
+          std::vector<double> v;
+          if ((st = close_generic(Eb, envr(j + 1), bond[j + 1], v))) return st;
+          for (size_t t = 0; t < pairs.size(); ++t)
+            if (pairs[t].first == i && pairs[t].second == j) vals[t] = v;
+        }
+        if (j < jmax) {
+          if ((st = left_step_to(j, Ea, Eb, false))) return st;
+          std::swap(Ea, Eb);
+        }
+      }
+    }
+    return MPDO_OK;
+  }
+  // left_step writing into a workspace buffer with env stride (sE, sT >= sEnv are used with stride sEnv)
+  mpdo_status left_step_to(int q, const C* E, C* out, bool z) { return left_step(q, E, out, z); }
+  mpdo_status close_generic(const C* E, const C* Rr, int d, std::vector<double>& re) { return close_(E, Rr, d, re); }
+
+  // <a| rho |b> element transfer for a, b in {0, 1} on every site
+  mpdo_status element_(int a, int bsel, std::vector<double>& re, std::vector<double>& im) {
+    C* Ea = wE;
+    C* Eb = wT;
+    mpdo_status st = one_env(Ea);
+    if (st) return st;
+    for (int q = 0; q < n; ++q) {
+      const int dl = bond[q], dn = kraus[q], dr = bond[q + 1];
+      const int N = dn * dr;
+      const C* A = site_ptr(q);
+      // tmp[l'][(n, r)] = sum_l E[l, l'] A[l, a, n, r]
+      st = gemm_(dl, N, dl, Ea, v2(sEnv, 0, 0, 1, 0, 0, dl), A + (int64_t)a * N, v2(slot_elems, 0, 0, 2 * N, 0, 0, 1),
+                 tmpA, row_major(N, sTmp));
+      if (st) return st;
+      // E'[r, r'] = sum_{(l', n)} tmp[(l', n), r] conj(A[l', b, n, r'])
+      st = gemm_(dr, dr, dl * dn, tmpA, v2(sTmp, 0, 0, 1, 0, 0, dr), A + (int64_t)bsel * N,
+                 v2(slot_elems, dn, (int64_t)2 * N, dr, 0, 0, 1, 1), Eb, row_major(dr, sEnv));
+      if (st) return st;
+      std::swap(Ea, Eb);
+    }
+    std::vector<C> hc(B);
+    for (int b = 0; b < B; ++b) CK(cudaMemcpyAsync(&hc[b], Ea + (int64_t)b * sEnv, sizeof(C), cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    re.resize(B);
+    im.resize(B);
+    for (int b = 0; b < B; ++b) {
+      re[b] = (double)hc[b].x;
+      im[b] = (double)hc[b].y;
+    }
+    return MPDO_OK;
+  }
+
+  // Tr rho^2 by the four-copy transfer (one chain at a time)
+  mpdo_status purity_(std::vector<double>& out) {
+    const int64_t X = chi_max, K = kappa_max;
+    const int64_t cap = (2 * K > 4 ? 2 * K : 4) * X * X * X * X;  // largest intermediate, elements
+    if ((double)cap * sizeof(C) > 16e9) return MPDO_ENOMEM;
+    const int64_t ecap = X * X * X * X;
+    if (pCap < cap) {
+      if (pX) cudaFree(pX);
+      if (pP) cudaFree(pP);
+      pX = pP = nullptr;
+      CK(dmalloc(&pX, cap));
+      CK(dmalloc(&pP, cap));
+      pCap = cap;
+    }
+    if (pECap < ecap) {
+      if (pE) cudaFree(pE);
+      if (pE2) cudaFree(pE2);
+      pE = pE2 = nullptr;
+      CK(dmalloc(&pE, ecap));
+      CK(dmalloc(&pE2, ecap));
+      pECap = ecap;
+    }
+    out.assign(B, 0);
+    for (int b = 0; b < B; ++b) {
+      CK(fill<R>(stream, 1, pE, mk<R>(1, 0)));
+      ++launches;
+      for (int q = 0; q < n; ++q) {
+        const int D = bond[q], dn = kraus[q], dr = bond[q + 1];
+        const C* A = site_ptr(q) + (int64_t)b * slot_elems;
+        const int64_t D3 = (int64_t)D * D * D;
+        const int PN = 2 * dn * dr;
+        // X1[(b,c,d)][(p,n,r)] = sum_a E[a][(b,c,d)] A[a][(p,n,r)]
+        mpdo_status st = gemm_((int)D3, PN, D, pE, v2(0, 0, 0, 1, 0, 0, D3), A, row_major(PN, 0), pX, row_major(PN, 0), 1);
+        if (st) return st;
+        // P1[c,d,p,r,b,n] from X1[b,c,d,p,n,r]
+        {
+          int dims[6] = {D, D, D, 2, dn, dr};
+          int perm[6] = {1, 2, 3, 5, 0, 4};
+          CK(permute<R>(stream, 1, 6, dims, perm, pX, 0, pP, 0));
+          ++launches;
+        }
+        // X2[(c,d,p,r)][(q,s)] = sum_{(b,n)} P1[(c,d,p,r)][(b,n)] conj(A[b,q,n,s])
+        const int64_t M2 = (int64_t)D * D * 2 * dr;
+        st = gemm_((int)M2, 2 * dr, D * dn, pP, row_major((int64_t)D * dn, 0), A,
+                   v2(0, dn, (int64_t)2 * dn * dr, dr, dr, (int64_t)dn * dr, 1, 1), pX, row_major(2 * dr, 0), 1);
+        if (st) return st;
+        // P2[d,p,r,s,c,q] from X2[c,d,p,r,q,s]
+        {
+          int dims[6] = {D, D, 2, dr, 2, dr};
+          int perm[6] = {1, 2, 3, 5, 0, 4};
+          CK(permute<R>(stream, 1, 6, dims, perm, pX, 0, pP, 0));
+          ++launches;
+        }
+        // X3[(d,p,r,s)][(m,t)] = sum_{(c,q)} P2[(d,p,r,s)][(c,q)] A[(c,q)][(m,t)]
+        const int64_t M3 = (int64_t)D * 2 * dr * dr;
+        st = gemm_((int)M3, dn * dr, 2 * D, pP, row_major(2 * D, 0), A, row_major((int64_t)dn * dr, 0), pX,
+                   row_major((int64_t)dn * dr, 0), 1);
+        if (st) return st;
+        // P3[r,s,t,d,p,m] from X3[d,p,r,s,m,t]
+        {
+          int dims[6] = {D, 2, dr, dr, dn, dr};
+          int perm[6] = {2, 3, 5, 0, 1, 4};
+          CK(permute<R>(stream, 1, 6, dims, perm, pX, 0, pP, 0));
+          ++launches;
+        }
+        // E'[(r,s,t)][u] = sum_{(d,p,m)} P3[(r,s,t)][(d,p,m)] conj(A[(d,p,m)][u])
+        const int64_t M4 = (int64_t)dr * dr * dr;
+        st = gemm_((int)M4, dr, D * 2 * dn, pP, row_major((int64_t)D * 2 * dn, 0), A, v2(0, 0, 0, dr, 0, 0, 1, 1), pE2,
+                   row_major(dr, 0), 1);
+        if (st) return st;
+        std::swap(pE, pE2);
+      }
+      C h;
+      CK(cudaMemcpyAsync(&h, pE, sizeof(C), cudaMemcpyDeviceToHost, stream));
+      CK(cudaStreamSynchronize(stream));
+      out[b] = (double)h.x;
+    }
+    return MPDO_OK;
+  }
+
+  mpdo_status expect(int kind, const int* args, int nargs, double* out) override {
+    if (capturing) return MPDO_ESTATE;
+    if (kind == MPDO_EXPECT_DISCARDED) {
+      CK(cudaMemcpyAsync(out, dDisc, sizeof(double) * 3 * B, cudaMemcpyDeviceToHost, stream));
+      CK(cudaStreamSynchronize(stream));
+      return MPDO_OK;
+    }
+    if (kind == MPDO_EXPECT_DIMS) {
+      for (int q = 1; q < n; ++q) out[q - 1] = bond[q];
+      for (int q = 0; q < n; ++q) out[n - 1 + q] = kraus[q];
+      return MPDO_OK;
+    }
+    mpdo_status st = build_envs();
+    if (st) return st;
+    std::vector<double> tr;
+    if ((st = trace_(tr))) return st;
+    auto finite = [&](double v) { return std::isfinite(v); };
+    if (kind == MPDO_EXPECT_TRACE) {
+      for (int b = 0; b < B; ++b) out[b] = tr[b];
+      return MPDO_OK;
+    }
+    if (kind == MPDO_EXPECT_ZZ || kind == MPDO_EXPECT_ZZ_MAP || kind == MPDO_EXPECT_MAXCUT) {
+      std::vector<std::pair<int, int>> pairs;
+      if (kind == MPDO_EXPECT_ZZ) {
+        if (nargs != 2 || !args) return MPDO_EINVAL;
+        int i = args[0], j = args[1];
+        if (i < 0 || j < 0 || i >= n || j >= n) return MPDO_EINVAL;
+        if (i == j) {
+          for (int b = 0; b < B; ++b) out[b] = 1.0;
+          return MPDO_OK;
+        }
+        pairs.push_back({i < j ? i : j, i < j ? j : i});
+      } else if (kind == MPDO_EXPECT_ZZ_MAP) {
+        for (int i = 0; i < n; ++i)
+          for (int j = i + 1; j < n; ++j) pairs.push_back({i, j});
+      } else {
+        if (nargs % 2 || (nargs && !args)) return MPDO_EINVAL;
+        for (int e = 0; e < nargs / 2; ++e) {
+          int i = args[2 * e], j = args[2 * e + 1];
+          if (i < 0 || j < 0 || i >= n || j >= n || i == j) return MPDO_EINVAL;
+          pairs.push_back({i < j ? i : j, i < j ? j : i});
+        }
+      }
+      std::vector<std::vector<double>> vals;
+      if ((st = zz_pairs(pairs, vals))) return st;
+      if (kind == MPDO_EXPECT_ZZ) {
+        for (int b = 0; b < B; ++b) out[b] = vals[0][b] / tr[b];
+      } else if (kind == MPDO_EXPECT_ZZ_MAP) {
+        for (int b = 0; b < B; ++b)
+          for (int i = 0; i < n; ++i) out[(int64_t)b * n * n + i * n + i] = 1.0;
+        for (size_t t = 0; t < pairs.size(); ++t)
+          for (int b = 0; b < B; ++b) {
+            double v = vals[t][b] / tr[b];
+            out[(int64_t)b * n * n + pairs[t].first * n + pairs[t].second] = v;
+            out[(int64_t)b * n * n + pairs[t].second * n + pairs[t].first] = v;
+          }
+      } else {
+        for (int b = 0; b < B; ++b) {
+          double s = 0;
+          for (size_t t = 0; t < pairs.size(); ++t) s += 0.5 * (1.0 - vals[t][b] / tr[b]);
+          out[b] = s;
+        }
+      }
+      for (int b = 0; b < B; ++b)
+        if (!finite(out[b])) return MPDO_ENOCONV;
+      return MPDO_OK;
+    }
+    if (kind == MPDO_EXPECT_GHZ) {
+      std::vector<double> r00, i00, r11, i11, r01, i01;
+      if ((st = element_(0, 0, r00, i00)) || (st = element_(1, 1, r11, i11)) || (st = element_(0, 1, r01, i01)))
+        return st;
+      for (int b = 0; b < B; ++b) {
+        out[b] = 0.5 * (r00[b] + r11[b] + 2 * r01[b]) / tr[b];
+        if (!finite(out[b])) return MPDO_ENOCONV;
+      }
+      return MPDO_OK;
+    }
+    if (kind == MPDO_EXPECT_PURITY) {
+      std::vector<double> p;
+      if ((st = purity_(p))) return st;
+      for (int b = 0; b < B; ++b) {
+        out[b] = p[b] / (tr[b] * tr[b]);
+        if (!finite(out[b])) return MPDO_ENOCONV;
+      }
+      return MPDO_OK;
+    }
+    return MPDO_EINVAL;
+  }
+
+  // put every site back into the slot and centre it had at capture begin (dims must match)
+  mpdo_status restore_layout() override {
+    for (int q = 0; q < n; ++q)
+      if (bond[q] != snap_bond[q] || kraus[q] != snap_kraus[q]) return MPDO_ESTATE;
+    mpdo_status st = move_centre(snap_centre);
+    if (st) return st;
+    // permutation of slots: copy site q from its current slot to snap_slot[q] through free slots
+    std::vector<int> cur = site_slot;
+    std::vector<int> owner(nslots, -1);
+    for (int q = 0; q < n; ++q) owner[cur[q]] = q;
+    for (int q = 0; q < n; ++q) {
+      int target = snap_slot[q];
+      if (cur[q] == target) continue;
+      // if target is occupied by site p, move p to a free slot first
+      int p = owner[target];
+      if (p >= 0) {
+        int f = -1;
+        for (int s = 0; s < nslots; ++s)
+          if (owner[s] < 0) {
+            f = s;
+            break;
+          }
+        CK(cudaMemcpyAsync(slot_ptr(f), slot_ptr(target), sizeof(C) * (size_t)B * slot_elems, cudaMemcpyDeviceToDevice,
+                           stream));
+        owner[f] = p;
+        owner[target] = -1;
+        cur[p] = f;
+      }
+      CK(cudaMemcpyAsync(slot_ptr(target), slot_ptr(cur[q]), sizeof(C) * (size_t)B * slot_elems,
+                         cudaMemcpyDeviceToDevice, stream));
+      owner[cur[q]] = -1;
+      owner[target] = q;
+      cur[q] = target;
+    }
+    site_slot = cur;
+    free_slots.clear();
+    for (int s = nslots - 1; s >= 0; --s)
+      if (owner[s] < 0) free_slots.push_back(s);
+    return MPDO_OK;
+  }
+
+  // ---------------------------------------------------------------- site access
+  mpdo_status get_site(int chain, int q, double* out) override {
+    const int64_t cnt = (int64_t)bond[q] * 2 * kraus[q] * bond[q + 1];
+    std::vector<C> h((size_t)cnt);
+    CK(cudaMemcpyAsync(h.data(), site_ptr(q) + (int64_t)chain * slot_elems, sizeof(C) * cnt, cudaMemcpyDeviceToHost,
+                       stream));
+    CK(cudaStreamSynchronize(stream));
+    for (int64_t i = 0; i < cnt; ++i) {
+      out[2 * i] = (double)h[i].x;
+      out[2 * i + 1] = (double)h[i].y;
+    }
+    return MPDO_OK;
+  }
+  mpdo_status set_site(int q, int dl, int dn, int dr, const double* data) override {
+    const int64_t cnt = (int64_t)dl * 2 * dn * dr;
+    std::vector<C> h((size_t)cnt * B);
+    for (int b = 0; b < B; ++b)
+      for (int64_t i = 0; i < cnt; ++i) h[b * cnt + i] = mk<R>((R)data[2 * (b * cnt + i)], (R)data[2 * (b * cnt + i) + 1]);
+    CK(cudaStreamSynchronize(stream));
+    for (int b = 0; b < B; ++b)
+      CK(cudaMemcpy(site_ptr(q) + (int64_t)b * slot_elems, h.data() + b * cnt, sizeof(C) * cnt, cudaMemcpyHostToDevice));
+    bond[q] = dl;
+    bond[q + 1] = dr;
+    kraus[q] = dn;
+    return MPDO_OK;
+  }
+
+  // ---------------------------------------------------------------- checkpoint
+  mpdo_status save(FILE* f) override {
+    std::vector<C> h((size_t)B * slot_elems);
+    for (int q = 0; q < n; ++q) {
+      CK(cudaMemcpyAsync(h.data(), site_ptr(q), sizeof(C) * h.size(), cudaMemcpyDeviceToHost, stream));
+      CK(cudaStreamSynchronize(stream));
+      if (fwrite(h.data(), sizeof(C), h.size(), f) != h.size()) return MPDO_EINVAL;
+    }
+    std::vector<double> d(3 * (size_t)B);
+    CK(cudaMemcpyAsync(d.data(), dDisc, sizeof(double) * d.size(), cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    if (fwrite(d.data(), sizeof(double), d.size(), f) != d.size()) return MPDO_EINVAL;
+    return MPDO_OK;
+  }
+  mpdo_status load(FILE* f) override {
+    std::vector<C> h((size_t)B * slot_elems);
+    for (int q = 0; q < n; ++q) {
+      if (fread(h.data(), sizeof(C), h.size(), f) != h.size()) return MPDO_EINVAL;
+      CK(cudaMemcpy(site_ptr(q), h.data(), sizeof(C) * h.size(), cudaMemcpyHostToDevice));
+    }
+    std::vector<double> d(3 * (size_t)B);
+    if (fread(d.data(), sizeof(double), d.size(), f) != d.size()) return MPDO_EINVAL;
+    CK(cudaMemcpy(dDisc, d.data(), sizeof(double) * d.size(), cudaMemcpyHostToDevice));
+    return MPDO_OK;
+  }
+};
+
+EngBase* make_engine(int prec) {
+  switch (prec) {
+    case MPDO_FP64: return new (std::nothrow) Eng<double, double>();
+    case MPDO_MIXED: return new (std::nothrow) Eng<float, double>();
+    case MPDO_FP32: return new (std::nothrow) Eng<float, float>();
+  }
+  return nullptr;
+}
+
+}  // namespace
+
+struct mpdo_ctx {
+  EngBase* e = nullptr;
+  ~mpdo_ctx() { delete e; }
+};
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char* mpdo_status_string(int s) {
+  switch (s) {
+    case MPDO_OK: return "ok";
+    case MPDO_EINVAL: return "invalid argument";
+    case MPDO_ENOMEM: return "out of memory";
+    case MPDO_ENOTCP: return "process matrix is not completely positive";
+    case MPDO_ENOTTP: return "process matrix is not trace preserving";
+    case MPDO_ENOCONV: return "non-finite result";
+    case MPDO_ETIMEOUT: return "timeout";
+    case MPDO_ECUDA: return "CUDA error";
+    case MPDO_ESTATE: return "invalid state for this call";
+  }
+  return "unknown status";
+}
+
+mpdo_status mpdo_init_batch(int batch, int n, int chi_max, int kappa_max, int prec, void* stream, mpdo_t* out) {
+  if (!out || batch < 1 || n < 1 || chi_max < 1 || kappa_max < 1 || batch > 65535) return MPDO_EINVAL;
+  if (4 * chi_max > 512 || 16 * kappa_max > 512) return MPDO_EINVAL;  // eigensolver size limit
+  if (prec != MPDO_FP64 && prec != MPDO_MIXED && prec != MPDO_FP32) return MPDO_EINVAL;
+  mpdo_ctx* h = new (std::nothrow) mpdo_ctx();
+  if (!h) return MPDO_ENOMEM;
+  h->e = make_engine(prec);
+  if (!h->e) {
+    delete h;
+    return MPDO_ENOMEM;
+  }
+  EngBase* e = h->e;
+  e->B = batch;
+  e->n = n;
+  e->chi_max = chi_max;
+  e->kappa_max = kappa_max;
+  e->prec = prec;
+  e->stream = (cudaStream_t)stream;
+  cudaGetDevice(&e->device);
+  mpdo_status st = e->alloc();
+  if (st) {
+    cudaError_t le = e->last_err;
+    delete h;
+    return le == cudaErrorMemoryAllocation ? MPDO_ENOMEM : st;
+  }
+  *out = h;
+  return MPDO_OK;
+}
+
+mpdo_status mpdo_init(int n, int chi_max, int kappa_max, int prec, void* stream, mpdo_t* out) {
+  return mpdo_init_batch(1, n, chi_max, kappa_max, prec, stream, out);
+}
+
+mpdo_status mpdo_free(mpdo_t h) {
+  if (!h) return MPDO_EINVAL;
+  if (h->e && h->e->capturing) return MPDO_ESTATE;
+  if (h->e) cudaStreamSynchronize(h->e->stream);
+  delete h;
+  return MPDO_OK;
+}
+
+mpdo_status mpdo_reset(mpdo_t h) {
+  if (!h) return MPDO_EINVAL;
+  return h->e->reset();
+}
+
+mpdo_status mpdo_sync(mpdo_t h) {
+  if (!h) return MPDO_EINVAL;
+  if (h->e->capturing) return MPDO_ESTATE;
+  return h->e->sync();
+}
+
+mpdo_status channel_set_from_process_matrices(mpdo_t h, int nq, int count, const double* chi, double tol,
+                                              mpdo_chan_t* out, int* n_kraus) {
+  if (!h || !out || !chi || count < 1 || (nq != 1 && nq != 2)) return MPDO_EINVAL;
+  if (h->e->capturing) return MPDO_ESTATE;
+  if (!(tol > 0)) tol = 1e-12;
+  const int d = 1 << nq, d2 = d * d;
+  const int64_t per = (int64_t)d2 * d2;
+  // host checks: finite, Hermitian, trace 1
+  for (int c = 0; c < count; ++c) {
+    const double* X = chi + 2 * per * c;
+    double tr_re = 0, tr_im = 0;
+    for (int a = 0; a < d2; ++a)
+      for (int b = 0; b < d2; ++b) {
+        double re = X[2 * (a * d2 + b)], im = X[2 * (a * d2 + b) + 1];
+        double re2 = X[2 * (b * d2 + a)], im2 = X[2 * (b * d2 + a) + 1];
+        if (!std::isfinite(re) || !std::isfinite(im)) return MPDO_EINVAL;
+        if (std::fabs(re - re2) > 1e-10 || std::fabs(im + im2) > 1e-10) return MPDO_EINVAL;
+        if (a == b) {
+          tr_re += re;
+          tr_im += im;
+        }
+      }
+    if (std::fabs(tr_re - 1.0) > 1e-8 || std::fabs(tr_im) > 1e-8) return MPDO_ENOTTP;
+  }
+  cudaStream_t s = h->e->stream;
+  cplx<double>*dchi = nullptr, *dchoi = nullptr, *dvec = nullptr;
+  double *deta = nullptr, *dscr = nullptr, *derr = nullptr;
+  int* dr = nullptr;
+  const int64_t scr = eig_scratch_elems(d2, d2);
+  mpdo_status ret = MPDO_OK;
+  std::unique_ptr<mpdo_chanset> cs(new (std::nothrow) mpdo_chanset());
+  if (!cs) return MPDO_ENOMEM;
+  std::vector<double> eta((size_t)count * d2);
+  std::vector<int> ranks(count);
+  int rmax = 1;
+  auto fail = [&](mpdo_status st) {
+    ret = st;
+    return st;
+  };
+  do {
+    if (cudaMalloc((void**)&dchi, sizeof(cplx<double>) * per * count) != cudaSuccess ||
+        cudaMalloc((void**)&dchoi, sizeof(cplx<double>) * per * count) != cudaSuccess ||
+        cudaMalloc((void**)&dvec, sizeof(cplx<double>) * per * count) != cudaSuccess ||
+        cudaMalloc((void**)&deta, sizeof(double) * d2 * count) != cudaSuccess ||
+        cudaMalloc((void**)&dscr, sizeof(double) * scr * count) != cudaSuccess ||
+        cudaMalloc((void**)&derr, sizeof(double) * count) != cudaSuccess ||
+        cudaMalloc((void**)&dr, sizeof(int) * count) != cudaSuccess) {
+      fail(MPDO_ENOMEM);
+      break;
+    }
+    if (cudaMemcpyAsync(dchi, chi, sizeof(cplx<double>) * per * count, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        chi_to_choi(s, count, nq, dchi, dchoi) != cudaSuccess) {
+      fail(MPDO_ECUDA);
+      break;
+    }
+    EigArgs<double> a;
+    a.A = dchoi;
+    a.astride = per;
+    a.n = d2;
+    a.k = d2;
+    a.w = deta;
+    a.wstride = d2;
+    a.V = dvec;
+    a.vv = col_major(d2, per);
+    a.scratch = dscr;
+    a.sstride = scr;
+    a.disc = nullptr;
+    a.gap = nullptr;
+    a.disc_stride = 0;
+    if (heevk<double>(s, count, a) != cudaSuccess ||
+        cudaMemcpyAsync(eta.data(), deta, sizeof(double) * d2 * count, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      fail(MPDO_ECUDA);
+      break;
+    }
+    h->e->launches += 2;
+    for (int c = 0; c < count && !ret; ++c) {
+      const double* w = &eta[(size_t)c * d2];
+      double neg = 0, emax = w[0] > 0 ? w[0] : 0;
+      for (int i = 0; i < d2; ++i)
+        if (w[i] < 0) neg -= w[i];
+      if (neg > 1e-8) {
+        fail(MPDO_ENOTCP);
+        break;
+      }
+      int r = 0;
+      for (int i = 0; i < d2; ++i)
+        if (w[i] > tol * emax && w[i] > 0) ++r;
+      if (r < 1) r = 1;
+      ranks[c] = r;
+      rmax = r > rmax ? r : rmax;
+    }
+    if (ret) break;
+    if (cudaMalloc((void**)&cs->kraus, sizeof(cplx<double>) * (size_t)count * rmax * d * d) != cudaSuccess) {
+      fail(MPDO_ENOMEM);
+      break;
+    }
+    std::vector<double> err(count);
+    if (cudaMemcpyAsync(dr, ranks.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        choi_to_kraus(s, count, nq, rmax, dr, deta, dvec, cs->kraus) != cudaSuccess ||
+        kraus_tp_error(s, count, nq, rmax, cs->kraus, derr) != cudaSuccess ||
+        cudaMemcpyAsync(err.data(), derr, sizeof(double) * count, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      fail(MPDO_ECUDA);
+      break;
+    }
+    h->e->launches += 2;
+    for (int c = 0; c < count; ++c)
+      if (!(err[c] <= 1e-8)) {
+        fail(MPDO_ENOTTP);
+        break;
+      }
+  } while (0);
+  cudaFree(dchi);
+  cudaFree(dchoi);
+  cudaFree(dvec);
+  cudaFree(deta);
+  cudaFree(dscr);
+  cudaFree(derr);
+  cudaFree(dr);
+  if (ret) return ret;
+  cs->nq = nq;
+  cs->count = count;
+  cs->rpad = rmax;
+  cs->device = h->e->device;
+  cs->ranks = ranks;
+  if (n_kraus)
+    for (int c = 0; c < count; ++c) n_kraus[c] = ranks[c];
+  *out = cs.release();
+  return MPDO_OK;
+}
+
+mpdo_status channel_from_process_matrix(mpdo_t h, int nq, const double* chi, double tol, mpdo_chan_t* out,
+                                        int* n_kraus) {
+  return channel_set_from_process_matrices(h, nq, 1, chi, tol, out, n_kraus);
+}
+
+mpdo_status channel_kraus(mpdo_chan_t ch, int idx, double* out, int* r_pad) {
+  if (!ch || idx < 0 || idx >= ch->count || !out) return MPDO_EINVAL;
+  const int d = 1 << ch->nq;
+  const size_t cnt = (size_t)ch->rpad * d * d;
+  if (cudaMemcpy(out, ch->kraus + (int64_t)idx * cnt, sizeof(cplx<double>) * cnt, cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
+    return MPDO_ECUDA;
+  if (r_pad) *r_pad = ch->rpad;
+  return MPDO_OK;
+}
+
+mpdo_status channel_free(mpdo_chan_t ch) {
+  if (!ch) return MPDO_EINVAL;
+  cudaDeviceSynchronize();
+  delete ch;
+  return MPDO_OK;
+}
+
+mpdo_status apply_1q(mpdo_t h, int q, const double* U, mpdo_chan_t ch) {
+  if (!h || !U) return MPDO_EINVAL;
+  return h->e->apply(1, q, U, nullptr, ch, nullptr);
+}
+mpdo_status apply_2q(mpdo_t h, int q, const double* U, mpdo_chan_t ch) {
+  if (!h || !U) return MPDO_EINVAL;
+  return h->e->apply(2, q, U, nullptr, ch, nullptr);
+}
+mpdo_status apply_1q_batch(mpdo_t h, int q, const double* U_dev, mpdo_chan_t ch, const int* chan_idx_dev) {
+  if (!h || !U_dev) return MPDO_EINVAL;
+  return h->e->apply(1, q, nullptr, U_dev, ch, chan_idx_dev);
+}
+mpdo_status apply_2q_batch(mpdo_t h, int q, const double* U_dev, mpdo_chan_t ch, const int* chan_idx_dev) {
+  if (!h || !U_dev) return MPDO_EINVAL;
+  return h->e->apply(2, q, nullptr, U_dev, ch, chan_idx_dev);
+}
+mpdo_status truncate_kraus(mpdo_t h, int q, int kappa, double* discarded) {
+  if (!h) return MPDO_EINVAL;
+  if (discarded && h->e->capturing) return MPDO_ESTATE;
+  return h->e->truncate(q, kappa, discarded);
+}
+mpdo_status expect(mpdo_t h, int kind, const int* args, int nargs, double* out) {
+  if (!h || !out) return MPDO_EINVAL;
+  return h->e->expect(kind, args, nargs, out);
+}
+
+static const char kMagic[8] = {'M', 'P', 'D', 'O', 'C', 'K', 'P', '1'};
+
+mpdo_status mpdo_save(mpdo_t h, const char* path) {
+  if (!h || !path) return MPDO_EINVAL;
+  EngBase* e = h->e;
+  if (e->capturing) return MPDO_ESTATE;
+  // canonical layout: centre first to 0 is not needed; store dims and centre as they are
+  FILE* f = fopen(path, "wb");
+  if (!f) return MPDO_EINVAL;
+  int hdr[6] = {e->B, e->n, e->chi_max, e->kappa_max, e->prec, e->centre};
+  bool ok = fwrite(kMagic, 1, 8, f) == 8 && fwrite(hdr, sizeof(int), 6, f) == 6 &&
+            fwrite(e->bond.data(), sizeof(int), e->n + 1, f) == (size_t)e->n + 1 &&
+            fwrite(e->kraus.data(), sizeof(int), e->n, f) == (size_t)e->n;
+  mpdo_status st = ok ? e->save(f) : MPDO_EINVAL;
+  fclose(f);
+  return st;
+}
+
+mpdo_status mpdo_load(const char* path, void* stream, mpdo_t* out) {
+  if (!path || !out) return MPDO_EINVAL;
+  FILE* f = fopen(path, "rb");
+  if (!f) return MPDO_EINVAL;
+  char magic[8];
+  int hdr[6];
+  if (fread(magic, 1, 8, f) != 8 || std::memcmp(magic, kMagic, 8) != 0 || fread(hdr, sizeof(int), 6, f) != 6) {
+    fclose(f);
+    return MPDO_EINVAL;
+  }
+  mpdo_t h = nullptr;
+  mpdo_status st = mpdo_init_batch(hdr[0], hdr[1], hdr[2], hdr[3], hdr[4], stream, &h);
+  if (st) {
+    fclose(f);
+    return st;
+  }
+  EngBase* e = h->e;
+  e->centre = hdr[5];
+  bool ok = fread(e->bond.data(), sizeof(int), e->n + 1, f) == (size_t)e->n + 1 &&
+            fread(e->kraus.data(), sizeof(int), e->n, f) == (size_t)e->n;
+  st = ok ? e->load(f) : MPDO_EINVAL;
+  fclose(f);
+  if (st) {
+    mpdo_free(h);
+    return st;
+  }
+  *out = h;
+  return MPDO_OK;
+}
+
+mpdo_status mpdo_capture_begin(mpdo_t h) {
+  if (!h) return MPDO_EINVAL;
+  EngBase* e = h->e;
+  if (e->capturing) return MPDO_ESTATE;
+  if (e->stream == nullptr) return MPDO_ESTATE;  // the legacy stream cannot be captured
+  if (cudaStreamSynchronize(e->stream) != cudaSuccess) return MPDO_ECUDA;
+  e->snap_bond = e->bond;
+  e->snap_kraus = e->kraus;
+  e->snap_slot = e->slots();
+  e->snap_centre = e->centre;
+  if (cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MPDO_ECUDA;
+  e->capturing = true;
+  return MPDO_OK;
+}
+
+mpdo_status mpdo_capture_end(mpdo_t h, int restore, mpdo_graph_t* out) {
+  if (!h || !out) return MPDO_EINVAL;
+  EngBase* e = h->e;
+  if (!e->capturing) return MPDO_ESTATE;
+  mpdo_status st = MPDO_OK;
+  if (restore) st = e->restore_layout();
+  cudaGraph_t g = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(e->stream, &g);
+  e->capturing = false;
+  if (st) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (ce != cudaSuccess) return MPDO_ECUDA;
+  mpdo_graph* gr = new (std::nothrow) mpdo_graph();
+  if (!gr) {
+    cudaGraphDestroy(g);
+    return MPDO_ENOMEM;
+  }
+  gr->graph = g;
+  gr->stream = e->stream;
+  if (cudaGraphInstantiate(&gr->exec, g, 0) != cudaSuccess) {
+    delete gr;
+    return MPDO_ECUDA;
+  }
+  *out = gr;
+  return MPDO_OK;
+}
+
+mpdo_status mpdo_graph_launch(mpdo_graph_t g) {
+  if (!g) return MPDO_EINVAL;
+  return cudaGraphLaunch(g->exec, g->stream) == cudaSuccess ? MPDO_OK : MPDO_ECUDA;
+}
+
+mpdo_status mpdo_graph_free(mpdo_graph_t g) {
+  if (!g) return MPDO_EINVAL;
+  cudaStreamSynchronize(g->stream);
+  delete g;
+  return MPDO_OK;
+}
+
+mpdo_status mpdo_get_site(mpdo_t h, int chain, int q, double* out, int* dims) {
+  if (!h || !out) return MPDO_EINVAL;
+  EngBase* e = h->e;
+  if (e->capturing) return MPDO_ESTATE;
+  if (chain < 0 || chain >= e->B || q < 0 || q >= e->n) return MPDO_EINVAL;
+  if (dims) {
+    dims[0] = e->bond[q];
+    dims[1] = e->kraus[q];
+    dims[2] = e->bond[q + 1];
+  }
+  return e->get_site(chain, q, out);
+}
+
+mpdo_status mpdo_set_site(mpdo_t h, int q, int dl, int dn, int dr, const double* data) {
+  if (!h || !data) return MPDO_EINVAL;
+  EngBase* e = h->e;
+  if (e->capturing) return MPDO_ESTATE;
+  if (q < 0 || q >= e->n || dl < 1 || dn < 1 || dr < 1 || dl > e->chi_max || dr > e->chi_max || dn > e->kappa_max)
+    return MPDO_EINVAL;
+  if ((q == 0 && dl != 1) || (q == e->n - 1 && dr != 1)) return MPDO_EINVAL;
+  return e->set_site(q, dl, dn, dr, data);
+}
+
+mpdo_status mpdo_set_centre(mpdo_t h, int q) {
+  if (!h) return MPDO_EINVAL;
+  if (h->e->capturing) return MPDO_ESTATE;
+  if (q < 0 || q >= h->e->n) return MPDO_EINVAL;
+  h->e->centre = q;
+  return MPDO_OK;
+}
+
+long long mpdo_launch_count(mpdo_t h) { return h ? h->e->launches : -1; }
+
+}  // extern "C"

@@ -1,0 +1,443 @@
+// MPDO-specific kernels: chi -> Choi -> Kraus (Sec. III), noisy-gate fusion K_i = N_i U (Sec. II.C),
+// the single-qubit noisy-gate contraction with its new Kraus leg (Fig. 2c), the small tensors of the
+// two-site split, and helpers for readouts.  All batched over independent instances.
+#include "kernels.h"
+
+namespace mpdo {
+
+namespace {
+constexpr int NT = 256;
+
+__device__ __forceinline__ cplx<double> pauli1(int m, int i, int j) {
+  // I, X, Y, Z
+  if (m == 0) return mk<double>(i == j ? 1.0 : 0.0, 0.0);
+  if (m == 1) return mk<double>(i != j ? 1.0 : 0.0, 0.0);
+  if (m == 2) {
+    if (i == j) return mk<double>(0.0, 0.0);
+    return mk<double>(0.0, i == 0 ? -1.0 : 1.0);  // [[0, -i], [i, 0]]
+  }
+  return mk<double>(i == j ? (i == 0 ? 1.0 : -1.0) : 0.0, 0.0);
+}
+// element (i, j) of the Pauli string with index m (first qubit most significant)
+__device__ cplx<double> pauli_elem(int nq, int m, int i, int j) {
+  cplx<double> v = mk<double>(1.0, 0.0);
+  for (int q = 0; q < nq; ++q) {
+    int sh = nq - 1 - q;
+    v = v * pauli1((m >> (2 * sh)) & 3, (i >> sh) & 1, (j >> sh) & 1);
+  }
+  return v;
+}
+
+__global__ void chi_to_choi_kernel(int count, int nq, const cplx<double>* chi, cplx<double>* choi) {
+  const int d = 1 << nq, d2 = d * d;
+  const int c = blockIdx.x;
+  if (c >= count) return;
+  const cplx<double>* X = chi + (int64_t)c * d2 * d2;
+  cplx<double>* L = choi + (int64_t)c * d2 * d2;
+  for (int e = threadIdx.x; e < d2 * d2; e += blockDim.x) {
+    int a = e % d2, b = e / d2;  // column-major L[a + b d2]
+    int ai = a / d, aj = a % d, bi = b / d, bj = b % d;
+    cplx<double> acc = mk<double>(0, 0);
+    for (int m = 0; m < d2; ++m) {
+      cplx<double> sm = pauli_elem(nq, m, ai, aj);
+      if (sm.x == 0.0 && sm.y == 0.0) continue;
+      for (int n = 0; n < d2; ++n) {
+        cplx<double> sn = pauli_elem(nq, n, bi, bj);
+        if (sn.x == 0.0 && sn.y == 0.0) continue;
+        acc = acc + X[m * d2 + n] * sm * conjg(sn);
+      }
+    }
+    L[e] = acc;
+  }
+}
+
+__global__ void choi_to_kraus_kernel(int count, int nq, int rmax, const int* r_dev, const double* eta,
+                                     const cplx<double>* vecs, cplx<double>* kraus) {
+  const int d = 1 << nq, d2 = d * d;
+  const int c = blockIdx.x;
+  if (c >= count) return;
+  const int r = r_dev[c];
+  for (int e = threadIdx.x; e < rmax * d2; e += blockDim.x) {
+    int i = e / d2, a = e % d2;  // K_i[row][col] with a = row * d + col (row-major vec)
+    cplx<double> v = mk<double>(0, 0);
+    if (i < r) {
+      double s = sqrt(fmax(eta[(int64_t)c * d2 + i], 0.0));
+      v = s * vecs[(int64_t)c * d2 * d2 + a + (int64_t)i * d2];
+    }
+    kraus[(int64_t)c * rmax * d2 + e] = v;
+  }
+}
+
+__global__ void kraus_tp_kernel(int count, int nq, int rmax, const cplx<double>* kraus, double* err) {
+  const int d = 1 << nq, d2 = d * d;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= count) return;
+  const cplx<double>* K = kraus + (int64_t)c * rmax * d2;
+  double e = 0;
+  for (int a = 0; a < d; ++a)
+    for (int b = 0; b < d; ++b) {
+      cplx<double> s = mk<double>(a == b ? -1.0 : 0.0, 0.0);
+      for (int i = 0; i < rmax; ++i)
+        for (int t = 0; t < d; ++t) cfma_cj(s, K[i * d2 + t * d + a], K[i * d2 + t * d + b]);
+      e = fmax(e, sqrt(norm2(s)));
+    }
+  err[c] = e;
+}
+
+template <typename R>
+__global__ void fuse_kernel(FuseArgs<R> a) {
+  const int z = blockIdx.x;
+  const int d = 1 << a.nq, dd = d * d;
+  __shared__ cplx<double> Kh[16 * 16];
+  const cplx<double>* U = a.Udev ? a.Udev + (int64_t)z * dd : a.U;
+  const int ch = a.chan_idx ? a.chan_idx[z] : 0;
+  const cplx<double>* N = a.kraus + (int64_t)ch * a.chan_stride;
+  for (int e = threadIdx.x; e < a.rk * dd; e += blockDim.x) {
+    int k = e / dd, i = (e % dd) / d, j = e % d;
+    cplx<double> acc = mk<double>(0, 0);
+    for (int t = 0; t < d; ++t) cfma(acc, N[k * dd + i * d + t], U[t * d + j]);
+    Kh[e] = acc;
+    a.Khat[(int64_t)z * a.rk * dd + e] = mk<R>((R)acc.x, (R)acc.y);
+  }
+  __syncthreads();
+  if (a.nq == 2 && a.Rt) {
+    // Rt[(a,b)][(p1 p2)][(q1 q2)] = sum_{p2', k} Khat_k[(a p2'), (p1 p2)] conj(Khat_k[(b p2'), (q1 q2)])
+    for (int e = threadIdx.x; e < 64; e += blockDim.x) {
+      int ab = e / 16, pp = (e / 4) % 4, qq = e % 4;
+      int ra = ab / 2, rb = ab % 2;
+      cplx<double> acc = mk<double>(0, 0);
+      for (int k = 0; k < a.rk; ++k)
+        for (int p2 = 0; p2 < 2; ++p2)
+          cfma_cj(acc, Kh[k * 16 + (rb * 2 + p2) * 4 + qq], Kh[k * 16 + (ra * 2 + p2) * 4 + pp]);
+      a.Rt[(int64_t)z * 64 + e] = mk<R>((R)acc.x, (R)acc.y);
+    }
+  }
+}
+
+template <typename R>
+__global__ void apply1q_kernel(int dl, int dn, int dr, int rk, const cplx<R>* A, int64_t astride,
+                               const cplx<R>* Khat, cplx<R>* X, int64_t xstride) {
+  const int z = blockIdx.y;
+  const int64_t total = (int64_t)rk * dn * dl * 2 * dr;
+  const cplx<R>* Az = A + (int64_t)z * astride;
+  const cplx<R>* K = Khat + (int64_t)z * rk * 4;
+  cplx<R>* Xz = X + (int64_t)z * xstride;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int r = (int)(e % dr);
+    int64_t t = e / dr;
+    int pp = (int)(t % 2);
+    t /= 2;
+    int l = (int)(t % dl);
+    t /= dl;
+    int n = (int)(t % dn);
+    int k = (int)(t / dn);
+    cplx<R> a0 = Az[(((int64_t)l * 2 + 0) * dn + n) * dr + r];
+    cplx<R> a1 = Az[(((int64_t)l * 2 + 1) * dn + n) * dr + r];
+    cplx<R> v = mk<R>(0, 0);
+    cfma(v, K[k * 4 + pp * 2 + 0], a0);
+    cfma(v, K[k * 4 + pp * 2 + 1], a1);
+    Xz[e] = v;
+  }
+}
+
+template <typename R>
+__global__ void build_T_kernel(int dm, const cplx<R>* Rt, const cplx<R>* E, int64_t estride, cplx<R>* T,
+                               int64_t tstride) {
+  const int z = blockIdx.y;
+  const int C2 = 2 * dm;
+  const int64_t total = (int64_t)C2 * 2 * C2 * 2;
+  const cplx<R>* Rz = Rt + (int64_t)z * 64;
+  const cplx<R>* Ez = E + (int64_t)z * estride;
+  cplx<R>* Tz = T + (int64_t)z * tstride;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int b = (int)(e % 2);
+    int cp = (int)((e / 2) % C2);
+    int a = (int)((e / (2 * C2)) % 2);
+    int c = (int)(e / (4 * C2));
+    int p1 = c / dm, bb = c % dm, q1 = cp / dm, bbp = cp % dm;
+    cplx<R> acc = mk<R>(0, 0);
+    for (int p2 = 0; p2 < 2; ++p2)
+      for (int q2 = 0; q2 < 2; ++q2)
+        cfma(acc, Rz[(a * 2 + b) * 16 + (p1 * 2 + p2) * 4 + (q1 * 2 + q2)],
+             Ez[(int64_t)(bb * 2 + p2) * C2 + (bbp * 2 + q2)]);
+    Tz[e] = acc;
+  }
+}
+
+template <typename R>
+__global__ void build_Y_kernel(int kchi, int dm, int rk, const cplx<R>* Khat, const cplx<R>* H, int64_t hstride,
+                               cplx<R>* Y, int64_t ystride) {
+  const int z = blockIdx.y;
+  const int C2 = 2 * dm;
+  const int64_t total = (int64_t)kchi * 2 * rk * C2;
+  const cplx<R>* K = Khat + (int64_t)z * rk * 16;
+  const cplx<R>* Hz = H + (int64_t)z * hstride;
+  cplx<R>* Yz = Y + (int64_t)z * ystride;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int col = (int)(e % C2);
+    int64_t row = e / C2;
+    int k = (int)(row % rk);
+    int p2p = (int)((row / rk) % 2);
+    int bp = (int)(row / (2 * rk));
+    int bb = col / 2, p2 = col % 2;
+    cplx<R> acc = mk<R>(0, 0);
+    for (int p1p = 0; p1p < 2; ++p1p)
+      for (int p1 = 0; p1 < 2; ++p1)
+        cfma(acc, K[k * 16 + (p1p * 2 + p2p) * 4 + (p1 * 2 + p2)], Hz[(int64_t)(bp * 2 + p1p) * C2 + (p1 * dm + bb)]);
+    Yz[e] = acc;
+  }
+}
+
+template <typename R>
+__global__ void copy_view_kernel(int M, int N, const cplx<R>* in, View vin, cplx<R>* out, View vout) {
+  const int z = blockIdx.y;
+  const cplx<R>* I = in + view_batch(vin, z);
+  cplx<R>* O = out + view_batch(vout, z);
+  const int64_t total = (int64_t)M * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(e / N), j = (int)(e % N);
+    cplx<R> v = I[view_row(vin, i) + view_col(vin, j)];
+    if (vin.conj) v.y = -v.y;
+    if (vout.conj) v.y = -v.y;
+    O[view_row(vout, i) + view_col(vout, j)] = v;
+  }
+}
+
+template <typename R>
+__global__ void scale_odd_kernel(int64_t len, int64_t div, R sgn, cplx<R>* x, int64_t stride) {
+  cplx<R>* X = x + (int64_t)blockIdx.y * stride;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x)
+    if ((e / div) % 2 == 1) X[e] = sgn * X[e];
+}
+
+template <typename A, typename B>
+__global__ void convert_kernel(int64_t count, const cplx<A>* in, cplx<B>* out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = mk<B>((B)in[e].x, (B)in[e].y);
+}
+
+template <typename R>
+__global__ void init_zero_kernel(int count, cplx<R>* base, int64_t stride) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= count) return;
+  base[(int64_t)c * stride] = mk<R>(1, 0);
+  base[(int64_t)c * stride + 1] = mk<R>(0, 0);
+}
+
+template <typename R>
+__global__ void dot_kernel(int64_t len, const cplx<R>* a, int64_t astride, const cplx<R>* b, int64_t bstride,
+                           cplx<double>* out) {
+  __shared__ double rx[NT / 32], ry[NT / 32];
+  const int z = blockIdx.x;
+  const cplx<R>* A = a + (int64_t)z * astride;
+  const cplx<R>* B = b + (int64_t)z * bstride;
+  double sx = 0, sy = 0;
+  for (int64_t e = threadIdx.x; e < len; e += NT) {
+    cplx<R> u = A[e], v = B[e];
+    sx += (double)u.x * v.x + (double)u.y * v.y;
+    sy += (double)u.x * v.y - (double)u.y * v.x;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sx += __shfl_xor_sync(0xffffffffu, sx, o);
+    sy += __shfl_xor_sync(0xffffffffu, sy, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    rx[threadIdx.x >> 5] = sx;
+    ry[threadIdx.x >> 5] = sy;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tx = 0, ty = 0;
+    for (int w = 0; w < NT / 32; ++w) {
+      tx += rx[w];
+      ty += ry[w];
+    }
+    out[z] = mk<double>(tx, ty);
+  }
+}
+
+template <typename R>
+__global__ void fill_kernel(int64_t count, cplx<R>* x, cplx<R> v) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+    x[e] = v;
+}
+
+__global__ void init_disc_kernel(int batch, double* d) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= batch) return;
+  d[3 * b] = 0.0;
+  d[3 * b + 1] = 0.0;
+  d[3 * b + 2] = 1e300;
+}
+
+struct PermDesc {
+  int nd;
+  int dims[6];     // input dims (row-major)
+  int64_t ostr[6]; // output stride of each input dim
+};
+
+template <typename R>
+__global__ void permute_kernel(PermDesc p, int64_t total, const cplx<R>* in, int64_t istride, cplx<R>* out,
+                               int64_t ostride) {
+  const cplx<R>* I = in + (int64_t)blockIdx.y * istride;
+  cplx<R>* O = out + (int64_t)blockIdx.y * ostride;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t t = e, o = 0;
+    for (int q = p.nd - 1; q >= 0; --q) {
+      int64_t idx = t % p.dims[q];
+      t /= p.dims[q];
+      o += idx * p.ostr[q];
+    }
+    O[o] = I[e];
+  }
+}
+
+inline int grid_for(int64_t total) {
+  int64_t b = (total + NT - 1) / NT;
+  if (b < 1) b = 1;
+  if (b > 4096) b = 4096;
+  return (int)b;
+}
+}  // namespace
+
+cudaError_t chi_to_choi(cudaStream_t s, int count, int nq, const cplx<double>* chi, cplx<double>* choi) {
+  if (count <= 0) return cudaSuccess;
+  chi_to_choi_kernel<<<count, NT, 0, s>>>(count, nq, chi, choi);
+  return cudaGetLastError();
+}
+cudaError_t choi_to_kraus(cudaStream_t s, int count, int nq, int rmax, const int* r_dev, const double* eta,
+                          const cplx<double>* vecs, cplx<double>* kraus) {
+  if (count <= 0) return cudaSuccess;
+  choi_to_kraus_kernel<<<count, NT, 0, s>>>(count, nq, rmax, r_dev, eta, vecs, kraus);
+  return cudaGetLastError();
+}
+cudaError_t init_discarded(cudaStream_t s, int batch, double* d) {
+  if (batch <= 0) return cudaSuccess;
+  init_disc_kernel<<<(batch + 127) / 128, 128, 0, s>>>(batch, d);
+  return cudaGetLastError();
+}
+cudaError_t kraus_tp_error(cudaStream_t s, int count, int nq, int rmax, const cplx<double>* kraus, double* err) {
+  if (count <= 0) return cudaSuccess;
+  kraus_tp_kernel<<<(count + 63) / 64, 64, 0, s>>>(count, nq, rmax, kraus, err);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t fuse_gate(cudaStream_t s, int batch, const FuseArgs<R>& a) {
+  if (batch <= 0) return cudaSuccess;
+  if (a.rk > 16 || a.nq < 1 || a.nq > 2) return cudaErrorInvalidValue;
+  fuse_kernel<R><<<batch, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t apply_1q_kraus(cudaStream_t s, int batch, int dl, int dn, int dr, int rk, const cplx<R>* A,
+                           int64_t astride, const cplx<R>* Khat, cplx<R>* X, int64_t xstride) {
+  if (batch <= 0) return cudaSuccess;
+  int64_t total = (int64_t)rk * dn * dl * 2 * dr;
+  dim3 grid(grid_for(total), batch);
+  apply1q_kernel<R><<<grid, NT, 0, s>>>(dl, dn, dr, rk, A, astride, Khat, X, xstride);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t build_T(cudaStream_t s, int batch, int dm, const cplx<R>* Rt, const cplx<R>* E, int64_t estride,
+                    cplx<R>* T, int64_t tstride) {
+  if (batch <= 0) return cudaSuccess;
+  int64_t total = (int64_t)16 * dm * dm;
+  dim3 grid(grid_for(total), batch);
+  build_T_kernel<R><<<grid, NT, 0, s>>>(dm, Rt, E, estride, T, tstride);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t build_Y(cudaStream_t s, int batch, int kchi, int dm, int rk, const cplx<R>* Khat, const cplx<R>* H,
+                    int64_t hstride, cplx<R>* Y, int64_t ystride) {
+  if (batch <= 0) return cudaSuccess;
+  int64_t total = (int64_t)kchi * 2 * rk * 2 * dm;
+  dim3 grid(grid_for(total), batch);
+  build_Y_kernel<R><<<grid, NT, 0, s>>>(kchi, dm, rk, Khat, H, hstride, Y, ystride);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t copy_view(cudaStream_t s, int batch, int M, int N, const cplx<R>* in, View vin, cplx<R>* out, View vout) {
+  if (batch <= 0 || M <= 0 || N <= 0) return cudaSuccess;
+  dim3 grid(grid_for((int64_t)M * N), batch);
+  copy_view_kernel<R><<<grid, NT, 0, s>>>(M, N, in, vin, out, vout);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t scale_odd(cudaStream_t s, int batch, int64_t len, int64_t div, R sgn, cplx<R>* x, int64_t stride) {
+  if (batch <= 0 || len <= 0) return cudaSuccess;
+  dim3 grid(grid_for(len), batch);
+  scale_odd_kernel<R><<<grid, NT, 0, s>>>(len, div, sgn, x, stride);
+  return cudaGetLastError();
+}
+template <typename A, typename B>
+cudaError_t convert(cudaStream_t s, int64_t count, const cplx<A>* in, cplx<B>* out) {
+  if (count <= 0) return cudaSuccess;
+  convert_kernel<A, B><<<grid_for(count), NT, 0, s>>>(count, in, out);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t init_zero_sites(cudaStream_t s, int count, cplx<R>* base, int64_t stride) {
+  if (count <= 0) return cudaSuccess;
+  init_zero_kernel<R><<<(count + 127) / 128, 128, 0, s>>>(count, base, stride);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t dot_batch(cudaStream_t s, int batch, int64_t len, const cplx<R>* a, int64_t astride, const cplx<R>* b,
+                      int64_t bstride, cplx<double>* out) {
+  if (batch <= 0) return cudaSuccess;
+  dot_kernel<R><<<batch, NT, 0, s>>>(len, a, astride, b, bstride, out);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t fill(cudaStream_t s, int64_t count, cplx<R>* x, cplx<R> v) {
+  if (count <= 0) return cudaSuccess;
+  fill_kernel<R><<<grid_for(count), NT, 0, s>>>(count, x, v);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t permute(cudaStream_t s, int batch, int nd, const int* dims, const int* perm, const cplx<R>* in,
+                    int64_t istride, cplx<R>* out, int64_t ostride) {
+  if (batch <= 0 || nd < 1 || nd > 6) return nd > 6 ? cudaErrorInvalidValue : cudaSuccess;
+  PermDesc p{};
+  p.nd = nd;
+  int64_t total = 1;
+  for (int q = 0; q < nd; ++q) {
+    p.dims[q] = dims[q];
+    total *= dims[q];
+  }
+  // output dim j is input dim perm[j]; output is row-major over the permuted dims
+  int64_t st = 1;
+  for (int j = nd - 1; j >= 0; --j) {
+    p.ostr[perm[j]] = st;
+    st *= dims[perm[j]];
+  }
+  if (total == 0) return cudaSuccess;
+  dim3 grid(grid_for(total), batch);
+  permute_kernel<R><<<grid, NT, 0, s>>>(p, total, in, istride, out, ostride);
+  return cudaGetLastError();
+}
+
+#define INST(R)                                                                                                  \
+  template cudaError_t fuse_gate<R>(cudaStream_t, int, const FuseArgs<R>&);                                      \
+  template cudaError_t apply_1q_kraus<R>(cudaStream_t, int, int, int, int, int, const cplx<R>*, int64_t,        \
+                                         const cplx<R>*, cplx<R>*, int64_t);                                      \
+  template cudaError_t build_T<R>(cudaStream_t, int, int, const cplx<R>*, const cplx<R>*, int64_t, cplx<R>*,     \
+                                  int64_t);                                                                      \
+  template cudaError_t build_Y<R>(cudaStream_t, int, int, int, int, const cplx<R>*, const cplx<R>*, int64_t,     \
+                                  cplx<R>*, int64_t);                                                            \
+  template cudaError_t copy_view<R>(cudaStream_t, int, int, int, const cplx<R>*, View, cplx<R>*, View);          \
+  template cudaError_t scale_odd<R>(cudaStream_t, int, int64_t, int64_t, R, cplx<R>*, int64_t);                  \
+  template cudaError_t init_zero_sites<R>(cudaStream_t, int, cplx<R>*, int64_t);                                 \
+  template cudaError_t dot_batch<R>(cudaStream_t, int, int64_t, const cplx<R>*, int64_t, const cplx<R>*,         \
+                                    int64_t, cplx<double>*);                                                     \
+  template cudaError_t fill<R>(cudaStream_t, int64_t, cplx<R>*, cplx<R>);                                        \
+  template cudaError_t permute<R>(cudaStream_t, int, int, const int*, const int*, const cplx<R>*, int64_t,       \
+                                  cplx<R>*, int64_t);
+INST(float)
+INST(double)
+template cudaError_t convert<float, double>(cudaStream_t, int64_t, const cplx<float>*, cplx<double>*);
+template cudaError_t convert<double, float>(cudaStream_t, int64_t, const cplx<double>*, cplx<float>*);
+template cudaError_t convert<double, double>(cudaStream_t, int64_t, const cplx<double>*, cplx<double>*);
+template cudaError_t convert<float, float>(cudaStream_t, int64_t, const cplx<float>*, cplx<float>*);
+
+}  // namespace mpdo

@@ -1,0 +1,248 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, element by element.
+
+Tolerances: FP64 mode 1e-10 on every readout and density-matrix entry; the complex64 modes (MIXED,
+FP32) 1e-6 on readouts (the target accuracy of the mixed path) and 1e-5 on density-matrix entries.
+A truncated comparison is only asserted when the oracle's smallest relative eigenvalue gap at a cut
+is above 1e-9 (FP64) or 1e-5 (complex64): below it the kept subspace is not unique.
+"""
+import numpy as np
+import pytest
+
+from oracle import channels as OC
+from oracle import dense as OD
+from oracle import mpdo as OM
+from paper_2508_07610_gb300 import mpdo as G
+from paper_2508_07610_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": (1e-10, 1e-10, 1e-9), "mixed": (1e-6, 1e-5, 1e-5), "fp32": (1e-6, 1e-5, 1e-5)}  # readout, rho, gap
+
+
+def _oracle_from_gpu(st: G.MPDO, chain: int = 0) -> OM.MPDO:
+    o = OM.MPDO(st.n, st.chi_max, st.kappa_max)
+    o.sites = st.sites(chain)
+    return o
+
+
+def _check_state(st, orc, prec, n, chain=0, dense=True):
+    tol_r, tol_rho, tol_gap = TOL[prec]
+    if orc.min_gap < tol_gap:
+        pytest.skip(f"degenerate cut (gap {orc.min_gap:.2e})")
+    if dense:
+        rho_g = _oracle_from_gpu(st, chain).dense()
+        rho_o = orc.dense()
+        rho_g = rho_g / np.trace(rho_g)
+        rho_o = rho_o / np.trace(rho_o)
+        assert np.max(np.abs(rho_g - rho_o)) < tol_rho
+    assert abs(st.trace()[chain] - orc.trace()) < tol_r * max(1.0, orc.trace())
+    zz = st.zz_map()[chain]
+    zo = orc.zz_map()
+    assert np.max(np.abs(zz - zo)) < tol_r
+    assert abs(st.ghz_fidelity()[chain] - orc.ghz_fidelity()) < tol_r
+    disc = st.discarded()[chain]
+    assert abs(disc[0] - orc.discarded_chi) < max(tol_r, 1e-9)
+    assert abs(disc[1] - orc.discarded_kappa) < max(tol_r, 1e-9)
+
+
+# ------------------------------------------------------------------ chi -> Kraus (FP64 on the GPU)
+@pytest.mark.parametrize("nq,rank,seed", [(1, 1, 0), (1, 2, 1), (1, 4, 2), (2, 1, 3), (2, 5, 4), (2, 16, 5)])
+def test_chi_to_kraus_matches_oracle(nq, rank, seed):
+    rng = np.random.default_rng(seed)
+    chi = W.kraus_to_chi(W.random_channel_kraus(nq, rank, rng))
+    st = G.MPDO(2, 2, 2)
+    cs = st.channels(nq, [chi])
+    kg = cs.kraus(0)
+    ko = OC.chi_to_kraus(chi, nq)
+    assert cs.ranks[0] == len(ko) == rank
+    assert np.max(np.abs(OC.superop(list(kg)) - OC.superop(ko))) < 1e-12
+    assert OC.is_trace_preserving(list(kg), 1e-12)
+    # descending weight order (the pruning order of Sec. III)
+    w = [np.linalg.norm(K) ** 2 for K in kg]
+    assert all(w[i] >= w[i + 1] - 1e-12 for i in range(len(w) - 1))
+
+
+def test_chi_to_kraus_printed_depolarizing_and_set():
+    st = G.MPDO(2, 2, 2)
+    ps = [0.0, 1e-3, 0.1, 0.5]
+    chis = [np.diag([1 - 3 * p / 4, p / 4, p / 4, p / 4]).astype(complex) for p in ps]
+    cs = st.channels(1, chis)
+    assert list(cs.ranks) == [1, 4, 4, 4]
+    for i, p in enumerate(ps):
+        k = list(cs.kraus(i))
+        assert np.max(np.abs(OC.superop(k) - OC.superop(W.depolarizing_1q(p)))) < 1e-13
+
+
+def test_invalid_process_matrices_are_rejected():
+    st = G.MPDO(2, 2, 2)
+    good = W.kraus_to_chi(W.depolarizing_1q(0.1))
+    with pytest.raises(G.MPDOError) as e:
+        st.channels(1, [good * 1.1])
+    assert e.value.status == 4
+    bad = good.copy()
+    bad[0, 1] += 0.1
+    with pytest.raises(G.MPDOError) as e:
+        st.channels(1, [bad])
+    assert e.value.status == 1
+    with pytest.raises(G.MPDOError) as e:
+        st.channels(1, [np.diag([1.2, -0.2, 0, 0]).astype(complex)])
+    assert e.value.status == 3
+    with pytest.raises(G.MPDOError) as e:
+        st.channels(1, [np.full((4, 4), np.nan, complex)])
+    assert e.value.status == 1
+
+
+# ------------------------------------------------------------------ whole circuits
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp32"])
+def test_ghz_ansatz_n6(prec):
+    circ = W.ghz_ansatz()  # n = 6, depth 3, chi_max = 16, kappa_max = 4
+    st = G.run_circuit(circ, 16, 4, prec)
+    orc = OM.run_circuit(circ, 16, 4)
+    _check_state(st, orc, prec, 6)
+    tol_r = TOL[prec][0]
+    assert abs(st.purity()[0] - orc.purity()) < 10 * tol_r
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n,nops,chi,kap,seed", [(4, 14, 64, 64, 0), (5, 20, 3, 2, 1), (6, 24, 5, 3, 2),
+                                                  (7, 30, 4, 2, 3), (3, 12, 1, 1, 4), (2, 10, 2, 5, 5)])
+def test_random_circuits(prec, n, nops, chi, kap, seed):
+    rng = np.random.default_rng(1000 + seed)
+    circ = W.random_circuit(n, nops, rng, rank1=3, rank2=6)
+    st = G.run_circuit(circ, chi, kap, prec)
+    orc = OM.run_circuit(circ, chi, kap)
+    _check_state(st, orc, prec, n)
+
+
+def test_single_qubit_chain():
+    rng = np.random.default_rng(9)
+    circ = W.random_circuit(1, 6, rng, rank1=4, p2q=0.0)
+    st = G.run_circuit(circ, 4, 3, "fp64")
+    orc = OM.run_circuit(circ, 4, 3)
+    rho_g = _oracle_from_gpu(st).dense()
+    assert np.max(np.abs(rho_g / np.trace(rho_g) - orc.dense() / orc.trace())) < 1e-12
+
+
+def test_exact_when_caps_cover_ranks():
+    circ = W.ghz_ansatz(n=4, depth=2)
+    st = G.run_circuit(circ, 64, 64, "fp64")
+    rho = OD.run_circuit(circ)
+    rho_g = _oracle_from_gpu(st).dense()
+    assert np.max(np.abs(rho_g - rho)) < 1e-11
+    d = st.discarded()[0]
+    assert d[0] < 1e-13 and d[1] < 1e-13
+
+
+def test_readouts_match_dense_definitions():
+    circ = W.ghz_ansatz(n=5, depth=2)
+    st = G.run_circuit(circ, 8, 4, "fp64")
+    rho = _oracle_from_gpu(st).dense()
+    tr = np.trace(rho).real
+    assert abs(st.trace()[0] - tr) < 1e-11
+    edges = [(0, 1), (1, 4), (2, 3), (0, 3)]
+    assert abs(st.maxcut(edges)[0] - OD.maxcut_expectation(rho, 5, edges)) < 1e-11
+    assert abs(st.purity()[0] - OD.purity(rho)) < 1e-11
+    assert abs(st.ghz_fidelity()[0] - OD.ghz_fidelity(rho, 5)) < 1e-11
+    assert abs(st.zz(3, 1)[0] - OD.expect_zz(rho, 5, 1, 3)) < 1e-11
+
+
+# ------------------------------------------------------------------ batches
+def test_batch_with_per_chain_gates_and_channels():
+    torch = pytest.importorskip("torch")
+    B, n = 3, 4
+    rng = np.random.default_rng(77)
+    circs = [W.random_circuit(n, 0, rng) for _ in range(B)]
+    # one shared sequence of positions, different matrices and channels per chain
+    layout = [(1, 0), (1, 1), (2, 0), (1, 2), (2, 2), (2, 1), (1, 3), (2, 0), (1, 1)]
+    orcs = [OM.MPDO(n, 4, 3) for _ in range(B)]
+    st = G.MPDO(n, 4, 3, "fp64", batch=B, stream=torch.cuda.current_stream().cuda_stream)
+    keep = []
+    for kind, q in layout:
+        Us = [W.random_unitary(2 ** kind, rng) for _ in range(B)]
+        chans = [W.kraus_to_chi(W.random_channel_kraus(kind, 3 if kind == 1 else 5, rng)) for _ in range(B)]
+        cs = st.channels(kind, chans)
+        U_dev = torch.tensor(np.stack(Us), dtype=torch.complex128, device="cuda")
+        keep += [cs, U_dev]
+        (st.apply_1q_batch if kind == 1 else st.apply_2q_batch)(q, U_dev.data_ptr(), cs)
+        for b in range(B):
+            kr = OC.chi_to_kraus(chans[b], kind)
+            (orcs[b].apply_1q if kind == 1 else orcs[b].apply_2q)(q, Us[b], kr)
+    st.sync()
+    zz = st.zz_map()
+    for b in range(B):
+        rho_g = _oracle_from_gpu(st, b).dense()
+        rho_o = orcs[b].dense()
+        assert np.max(np.abs(rho_g / np.trace(rho_g) - rho_o / np.trace(rho_o))) < 1e-10
+        assert np.max(np.abs(zz[b] - orcs[b].zz_map())) < 1e-10
+
+
+def test_batch_channel_index_array():
+    torch = pytest.importorskip("torch")
+    B, n = 4, 3
+    rng = np.random.default_rng(5)
+    chans = [W.kraus_to_chi(W.random_channel_kraus(2, r, rng)) for r in (2, 5)]
+    idx = [1, 0, 0, 1]
+    st = G.MPDO(n, 4, 2, "fp64", batch=B, stream=torch.cuda.current_stream().cuda_stream)
+    cs = st.channels(2, chans)
+    U = W.random_unitary(4, rng)
+    U_dev = torch.tensor(np.stack([U] * B), dtype=torch.complex128, device="cuda")
+    idx_dev = torch.tensor(idx, dtype=torch.int32, device="cuda")
+    st.apply_2q_batch(0, U_dev.data_ptr(), cs, idx_dev.data_ptr())
+    st.apply_2q_batch(1, U_dev.data_ptr(), cs, idx_dev.data_ptr())
+    st.sync()
+    for b in range(B):
+        o = OM.MPDO(n, 4, 2)
+        kr = OC.chi_to_kraus(chans[idx[b]], 2)
+        o.apply_2q(0, U, kr)
+        o.apply_2q(1, U, kr)
+        rho_g = _oracle_from_gpu(st, b).dense()
+        assert np.max(np.abs(rho_g / np.trace(rho_g) - o.dense() / o.trace())) < 1e-10
+
+
+# ------------------------------------------------------------------ explicit truncation, checkpoint, graphs
+def test_truncate_kraus_explicit():
+    rng = np.random.default_rng(21)
+    circ = W.random_circuit(4, 16, rng, rank1=4, rank2=8)
+    st = G.run_circuit(circ, 8, 6, "fp64")
+    orc = OM.run_circuit(circ, 8, 6)
+    w = st.truncate_kraus(2, 2)[0]
+    wo = orc.truncate_kraus(2, 2)
+    assert abs(w - wo) < 1e-10
+    rho_g = _oracle_from_gpu(st).dense()
+    assert np.max(np.abs(rho_g / np.trace(rho_g) - orc.dense() / orc.trace())) < 1e-10
+
+
+def test_checkpoint_round_trip(tmp_path):
+    circ = W.ghz_ansatz(n=5, depth=2)
+    st = G.run_circuit(circ, 8, 3, "fp64")
+    path = str(tmp_path / "state.ckpt")
+    st.save(path)
+    st2 = G.MPDO.load(path)
+    assert st2.dims() == st.dims()
+    assert np.max(np.abs(st2.zz_map() - st.zz_map())) < 1e-14
+    assert np.max(np.abs(st2.discarded() - st.discarded())) < 1e-15
+    # the loaded state continues like the original
+    ch = st.channels(2, [W.kraus_to_chi(W.depolarizing_2q(0.02))])
+    ch2 = st2.channels(2, [W.kraus_to_chi(W.depolarizing_2q(0.02))])
+    st.apply_2q(1, W.cz(), ch)
+    st2.apply_2q(1, W.cz(), ch2)
+    assert np.max(np.abs(st2.zz_map() - st.zz_map())) < 1e-13
+
+
+def test_graph_capture_replays_circuit():
+    torch = pytest.importorskip("torch")
+    s = torch.cuda.Stream()
+    circ = W.ghz_ansatz(n=5, depth=2)
+    st = G.MPDO(5, 8, 3, "fp64", stream=s.cuda_stream)
+    chans = {c: st.channels(nq, [chi]) for c, (nq, chi) in enumerate(circ.chis)}
+    ref = G.run_circuit(circ, 8, 3, "fp64")
+    st.capture_begin()
+    st.reset()
+    for op in circ.ops:
+        (st.apply_1q if op.kind == 1 else st.apply_2q)(op.q, op.U, chans[op.chan])
+    g = st.capture_end()
+    for _ in range(2):
+        g.launch()
+        st.sync()
+        assert np.max(np.abs(st.zz_map() - ref.zz_map())) < 1e-13
+        assert np.max(np.abs(st.discarded() - ref.discarded())) < 1e-14
