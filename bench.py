@@ -1,0 +1,400 @@
+"""Throughput of the noisy two-qubit MPDO update on GB300.
+
+Metric: 2q gate+channel+truncate updates/s at chi=64, kappa=8 (batched complex64 path), on the
+steady-state workload of a 20-qubit hardware-efficient ansatz: every bond at chi_max = 64 and every
+Kraus leg at kappa_max = 8.  One step = one ansatz layer on every chain of the batch: Rz.Ry.Rz on all
+20 qubits, each with its amplitude-damping + depolarizing channel, then CZ on the bonds of one
+parity (10 or 9 per chain, alternating), each with a DEP2(p2) o ZZ(phi) channel of Kraus rank 16,
+including the bond split to chi_max and the Kraus-leg truncation to kappa_max.  `value` counts the
+2q updates only.  Channels are given as chi matrices and converted on the GPU before timing.
+
+Modes: default = this library on the GPU (graph-captured layers; inputs resident in HBM).
+--impl reference = the CPU reference (oracle) on this host's cores on a bounded sample.
+Multi-GPU (torchrun): every rank runs its own batch of chains ("replicas only": a chain does not
+shard); value = total updates of all ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_QUBITS, CHI, KAPPA = 20, 64, 8
+METRIC = "2q gate+channel+truncate updates/s at chi=64, kappa=8 (err<=1e-6 vs FP64); batched vs plain"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                parts = [p.strip() for p in out.stdout.strip().split(",")]
+                if len(parts) >= 8:
+                    self.samples.append(parts)
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[4 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------------------------------- workload
+def build_workload(B: int, seed: int, depth: int):
+    """Per-chain channels (per qubit and per pair) and per-chain 1q gate matrices for `depth` layers."""
+    from paper_2508_07610_gb300 import workloads as W
+
+    ss = np.random.SeedSequence(seed)
+    chis1 = [[None] * B for _ in range(N_QUBITS)]
+    chis2 = [[None] * B for _ in range(N_QUBITS - 1)]
+    U1 = np.zeros((depth, N_QUBITS, B, 2, 2), dtype=np.complex128)
+    for b, child in enumerate(ss.spawn(B)):
+        rng = np.random.default_rng(child)
+        chis, c1, c2 = W.hea_channels(N_QUBITS, rng)
+        for q in range(N_QUBITS):
+            chis1[q][b] = chis[c1[q]][1]
+        for q in range(N_QUBITS - 1):
+            chis2[q][b] = chis[c2[q]][1]
+        for layer in range(depth):
+            for q in range(N_QUBITS):
+                a, bb, c = rng.uniform(-math.pi, math.pi, size=3)
+                U1[layer, q, b] = W.rz(c) @ W.ry(bb) @ W.rz(a)
+    return chis1, chis2, U1
+
+
+class Runner:
+    """B chains on one GPU, channels converted on the GPU, gates resident in device memory."""
+
+    def __init__(self, B, prec, stream_ptr, seed, depth, torch):
+        from paper_2508_07610_gb300 import mpdo as G
+        from paper_2508_07610_gb300 import workloads as W
+
+        self.torch = torch
+        self.B = B
+        self.st = G.MPDO(N_QUBITS, CHI, KAPPA, prec, batch=B, stream=stream_ptr)
+        chis1, chis2, U1 = build_workload(B, seed, depth)
+        self.ch1 = [self.st.channels(1, chis1[q]) for q in range(N_QUBITS)]
+        self.ch2 = [self.st.channels(2, chis2[q]) for q in range(N_QUBITS - 1)]
+        self.U1_host = U1  # [layer][q][B][2][2]
+        self.U1 = torch.tensor(U1, dtype=torch.complex128, device="cuda")
+        cz = np.stack([W.cz()] * B)
+        self.CZ = torch.tensor(cz, dtype=torch.complex128, device="cuda")
+        self.depth = depth
+
+    def n2q(self, layer):
+        return len(range(layer % 2, N_QUBITS - 1, 2))
+
+    def layer(self, layer, U1=None):
+        """One ansatz layer in a single left-to-right sweep (gates on disjoint qubits commute)."""
+        st = self.st
+        U1 = self.U1 if U1 is None else U1
+        li = layer % self.depth
+        par = layer % 2
+        for q in range(N_QUBITS):
+            st.apply_1q_batch(q, U1[li, q].data_ptr(), self.ch1[q])
+            if q >= 1 and (q - 1) % 2 == par and q - 1 < N_QUBITS - 1:
+                st.apply_2q_batch(q - 1, self.CZ.data_ptr(), self.ch2[q - 1])
+
+
+def run_ours(args, torch, rank, world):
+    from paper_2508_07610_gb300 import build as Bld
+
+    Bld.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    B = args.chains
+    depth = 2
+    seed = 0x2508076100 + 2 + 1000 * rank
+    r = Runner(B, args.prec, sp, seed, depth, torch)
+    st = r.st
+    # ---- reach the steady state: every bond at chi = 64 and every Kraus leg at kappa = 8
+    for layer in range(args.saturate):
+        r.layer(layer)
+    st.sync()
+    bonds, kraus = st.dims()
+    assert min(bonds[4:-4]) == CHI and min(kraus) == KAPPA, (bonds, kraus)
+    zz_fast = st.zz_map()[0]
+    # ---- capture the even and the odd layer; the graphs put the centre and storage back on exit
+    graphs, per_graph = [], []
+    for layer in (0, 1):
+        c0 = st.launch_count()
+        st.capture_begin()
+        r.layer(layer)
+        graphs.append(st.capture_end(restore=True))
+        per_graph.append(st.launch_count() - c0)
+    # ---- warm-up
+    for s in range(args.warmup):
+        graphs[s % 2].launch()
+    st.sync()
+    lc0 = st.launch_count()
+    # ---- timed region
+    barrier(torch, world)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n2q = 0
+    with ClockSampler(dev.index) as clk:
+        ev0.record(stream)
+        for s in range(args.steps):
+            graphs[s % 2].launch()
+            n2q += r.n2q(s) * B
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    barrier(torch, world)
+    launches = sum(per_graph[s % 2] for s in range(args.steps))
+    ms_max = allreduce_max(torch, world, ms)
+    total_2q = allreduce_sum(torch, world, n2q)
+    value = total_2q / (ms_max / 1e3)
+    # ---- accuracy check of the steady-state mixed path: one more layer on a 1-chain FP64 twin
+    # is done in the tests; here report the discarded weights and a readout for context
+    disc = st.discarded()
+    # ---- per-kernel-class timing of the same layers (CUDA events around every launch, no graph)
+    st.profile(True)
+    for s in range(2):
+        r.layer(s)
+    prof = st.profile_read()
+    st.profile(False)
+    # ---- end-to-end through the C ABI from host buffers: H2D of the step's gate matrices from
+    # pinned memory, the layer through the public calls, D2H of the step's result (discarded weights)
+    pinned = torch.empty(r.U1.shape, dtype=torch.complex128, pin_memory=True)
+    pinned.copy_(torch.from_numpy(r.U1_host))
+    Udev = torch.empty_like(r.U1)
+    e2e_steps = max(2, min(args.steps, 6))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_2q = 0
+    for s in range(e2e_steps):
+        li = s % depth
+        with torch.cuda.stream(stream):
+            Udev[li].copy_(pinned[li], non_blocking=True)
+        r.layer(s, U1=Udev)
+        _ = st.discarded()
+        e2e_2q += r.n2q(s) * B
+    t_e2e = time.perf_counter() - t0
+    e2e_val = allreduce_sum(torch, world, e2e_2q) / allreduce_max(torch, world, t_e2e)
+    h2d = int(pinned[0].numel() * 16)
+    d2h = 3 * 8 * B
+    # ---- plain path: one chain, complex128, launch by launch
+    plain = None
+    err = None
+    if rank == 0 and args.plain_steps > 0:
+        # the same gates and channels as chain 0 of the batch, in complex128 with FP64 eigensolvers
+        rp = Runner(1, "fp64", sp, seed, depth, torch)
+        for layer in range(args.saturate):
+            rp.layer(layer)
+        rp.st.sync()
+        err = float(np.max(np.abs(rp.st.zz_map()[0] - zz_fast)))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cnt = 0
+        for s in range(args.plain_steps):
+            rp.layer(s)
+            cnt += rp.n2q(s)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plain = cnt / (e0.elapsed_time(e1) / 1e3)
+        del rp
+    return {
+        "value": value, "ms": ms_max, "n2q": total_2q, "disc": disc, "prof": prof, "e2e": e2e_val,
+        "h2d": h2d, "d2h": d2h, "clocks": clk.summary(), "plain": plain,
+        "launches": launches, "B": B, "err": err,
+    }
+
+
+def barrier(torch, world):
+    if world > 1:
+        torch.distributed.barrier()
+
+
+def allreduce_max(torch, world, x):
+    if world == 1:
+        return x
+    t = torch.tensor([float(x)], device="cuda")
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allreduce_sum(torch, world, x):
+    if world == 1:
+        return x
+    t = torch.tensor([float(x)], device="cuda")
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------------------- CPU reference
+def cpu_reference_sample(updates: int = 1, seed: int = 11):
+    """Time the CPU reference on `updates` 2q updates of a saturated n=20, chi=64, kappa=8 chain
+    (random right-canonical state, CZ + DEP2(1e-2) o ZZ channel, rank 16), centre moves included."""
+    from oracle import channels as OC
+    from oracle import mpdo as OM
+    from paper_2508_07610_gb300 import workloads as W
+
+    rng = np.random.default_rng(seed)
+    o = OM.MPDO(N_QUBITS, CHI, KAPPA)
+    o.sites = W.random_right_canonical_sites(N_QUBITS, CHI, KAPPA, rng)
+    o.centre = 0
+    kr = OC.chi_to_kraus(W.kraus_to_chi(W.compose(W.depolarizing_2q(1e-2), W.unitary_channel(W.zz_phase(0.01)))), 2)
+    q0 = N_QUBITS // 2 - 1
+    o.move_centre(q0)
+    t0 = time.perf_counter()
+    for u in range(updates):
+        o.apply_2q(q0 + 2 * u, W.cz(), kr)
+        if u + 1 < updates:
+            o.move_centre(q0 + 2 * (u + 1))
+    dt = time.perf_counter() - t0
+    return updates / dt, dt
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=4)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--chains", type=int, default=64)
+    ap.add_argument("--saturate", type=int, default=12)
+    ap.add_argument("--plain-steps", type=int, default=1)
+    ap.add_argument("--cpu-updates", type=int, default=1)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp32", "fp64"])
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+
+    cfg = {"workload": "HEA n=20 steady state (chi=64 on every bond, kappa=8 on every Kraus leg), "
+                       "layer = 20 noisy Rz.Ry.Rz + 10/9 noisy CZ (DEP2 o ZZ, Kraus rank 16)",
+           "n_qubits": N_QUBITS, "chi_max": CHI, "kappa_max": KAPPA}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        steps_done, t_tot = 0, 0.0
+        for s in range(args.warmup + args.steps):
+            ups, dt = cpu_reference_sample(1, seed=11 + s)
+            if s >= args.warmup:
+                steps_done += 1
+                t_tot += dt
+        v = steps_done / t_tot
+        cfg.update({"chains_per_gpu": 1, "sample": "one 2q update per step"})
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "updates/s", "n_gpus": 0,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / max(steps_done, 1),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+                "data": "synthetic", "config": cfg,
+                "cpu_baseline": {"value": v, "unit": "updates/s", "cores": host_cores(), "kind": "oracle",
+                                 "sample": "one 2q update per step on a random right-canonical n=20 chain"},
+                "e2e": {"value": v, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+
+    if world > 1:
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        torch.distributed.init_process_group("nccl")
+    res = run_ours(args, torch, rank, world)
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    pk, src = peaks()
+    # dominant kernel class by time
+    prof = res["prof"]
+    dom = max(prof, key=lambda k: prof[k][0])
+    ms_d, fl_d, cnt_d = prof[dom]
+    # complex64 arithmetic on CUDA cores: FP32 FMA pipe peak = 152 SMs x 128 lanes x 2 flops x max clock
+    fp32_peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    achieved = (fl_d / (ms_d / 1e3)) / 1e12 if ms_d > 0 else 0.0
+    roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": None,
+                "peak_source": f"FP32 CUDA-core peak from unit counts x {pk.get('sm_max_mhz', 2070.0):.0f} MHz "
+                               f"({src} peaks file has no FP32 entry)",
+                "classes": {k: {"ms": v[0], "tflops": (v[1] / (v[0] / 1e3) / 1e12) if v[0] > 0 else None,
+                                "launches": v[2]} for k, v in prof.items()}}
+    cpu = None
+    if not args.no_cpu:
+        try:
+            v, dt = cpu_reference_sample(args.cpu_updates)
+            cpu = {"value": v, "unit": "updates/s", "cores": host_cores(), "kind": "oracle",
+                   "sample": f"{args.cpu_updates} 2q update(s) of a random right-canonical n=20 chi=64 kappa=8 chain, "
+                             f"{dt:.1f} s"}
+        except Exception as e:  # report, never fall back
+            cpu = {"value": None, "unit": "updates/s", "cores": host_cores(), "kind": "oracle",
+                   "sample": f"failed: {e}"}
+    prec_desc = {"mixed": "complex64 contractions, FP64 eigensolvers (MIXED)",
+                 "fp32": "complex64 contractions, FP32 eigensolvers", "fp64": "complex128, FP64 eigensolvers"}
+    cfg.update({"chains_per_gpu": res["B"], "precision": prec_desc[args.prec],
+                "max_abs_zz_err_vs_fp64_after_saturation": res["err"],
+                "l2": "state and workspaces (~GBs) far exceed the 129 MB L2",
+                "plain_fp64_updates_per_s": res["plain"], "graph_captured": True})
+    line = {"metric": METRIC, "value": res["value"], "unit": "updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["ms"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128" if args.prec == "fp64" else "c64",
+            "data": "synthetic", "config": cfg,
+            "clocks": res["clocks"],
+            "e2e": {"value": res["e2e"], "unit": "updates/s", "h2d_bytes_per_step": res["h2d"],
+                    "d2h_bytes_per_step": res["d2h"]},
+            "gpu_launches": res["launches"], "roofline": roofline, "cpu_baseline": cpu}
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

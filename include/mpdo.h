@@ -133,6 +133,14 @@ mpdo_status mpdo_get_site(mpdo_t h, int chain, int q, double* out, int* dims);
 mpdo_status mpdo_set_site(mpdo_t h, int q, int dl, int dn, int dr, const double* data);
 mpdo_status mpdo_set_centre(mpdo_t h, int q);
 
+/* Per-launch CUDA-event timing by kernel class (0 GEMM, 1 QR, 2 eigensolver, 3 other), for
+ * measurement: enable records an event pair around every launch made outside graph capture;
+ * read synchronises and returns, per class, the summed milliseconds, the summed algorithmic
+ * flops the engine attributes to those launches (8 real flops per complex multiply-add) and the
+ * launch count (arrays of 4), then clears the record. */
+mpdo_status mpdo_profile(mpdo_t h, int enable);
+mpdo_status mpdo_profile_read(mpdo_t h, double* ms, double* flops, long long* count);
+
 /* Number of kernels the library launched on this handle since creation (for accounting). */
 long long mpdo_launch_count(mpdo_t h);
 const char* mpdo_status_string(int status);

@@ -46,6 +46,7 @@ class MPDO:
         self.discarded_chi = 0.0
         self.discarded_kappa = 0.0
         self.min_gap = np.inf   # smallest (s_k^2 - s_{k+1}^2)/s_1^2 over truncations that cut
+        self.cuts = []          # (relative gap, s_k^2 / s_1^2) of every truncation that cuts
         self.log = []           # (kind, site, kept, available, discarded weight)
 
     # ------------------------------------------------------------ canonical form
@@ -82,8 +83,16 @@ class MPDO:
         k = max(1, min(cap, nz))
         dropped = float(np.sum(s[k:] ** 2)) / total
         if k < nz:
-            self.min_gap = min(self.min_gap, float((s[k - 1] ** 2 - s[k] ** 2) / s[0] ** 2))
+            gap = float((s[k - 1] ** 2 - s[k] ** 2) / s[0] ** 2)
+            self.min_gap = min(self.min_gap, gap)
+            self.cuts.append((gap, float(s[k - 1] ** 2 / s[0] ** 2)))
         return k, dropped
+
+    def cut_sensitivity(self, eps: float) -> float:
+        """First-order bound on how far a readout can move when every truncation's Gram matrix is
+        perturbed by eps (relative to its largest eigenvalue): a perturbation rotates the last kept
+        and first dropped directions by about min(1, eps / gap), which moves weight s_k^2 / s_1^2."""
+        return float(sum(min(1.0, eps / g) * w if g > 0 else w for g, w in self.cuts))
 
     def truncate_kraus(self, q: int, kappa: int = 0) -> float:
         """Eq. (svdNoise): T as a (p, l, r) x n matrix = U S V^dag; keep the top kappa; T' = T V."""

@@ -48,6 +48,15 @@ __host__ __device__ __forceinline__ void cfma_cj(cplx<R>& acc, cplx<R> a, cplx<R
   acc.y = fma(-a.y, b.x, acc.y);
 }
 
+// Norms below this are treated as exact zeros by the Householder steps, so that 1 / (|x| (|x| + |a|))
+// cannot overflow (its square stays far above the smallest normal number).
+template <typename R>
+__host__ __device__ __forceinline__ R tiny_norm();
+template <>
+__host__ __device__ __forceinline__ float tiny_norm<float>() { return 1e-17f; }
+template <>
+__host__ __device__ __forceinline__ double tiny_norm<double>() { return 1e-140; }
+
 // A 2-D view of a strided tensor.  Logical (row i, col j) of batch item z lives at
 //   off(z) + (i / rdiv) * rhi + (i % rdiv) * rlo + (j / cdiv) * chi + (j % cdiv) * clo
 // where off(z) = (z / bdiv) * bhi + (z % bdiv) * blo.  A divisor of 0 means "no split"

@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(NT) heevk_kernel(EigArgs<R> g) {
     const R aa = sqrt(norm2(a));
     const R nrm = sqrt(aa * aa + s);
     const cplx<R> ph = (aa > R(0)) ? mk<R>(a.x / aa, a.y / aa) : mk<R>(1, 0);
-    const R beta = (nrm > R(0)) ? R(1) / (nrm * (nrm + aa)) : R(0);
+    const R beta = (nrm > tiny_norm<R>()) ? R(1) / (nrm * (nrm + aa)) : R(0);
     const cplx<R> v0 = a + nrm * ph;
     for (int i = j + 1 + tid; i < n; i += NT) s_v[i] = (i == j + 1) ? v0 : col[i];
     if (tid == 0) s_beta[j] = beta;
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(NT) heevk_kernel(EigArgs<R> g) {
     }
     __syncthreads();
     if (tid == 0) {
-      col[j + 1] = (nrm > R(0)) ? mk<R>(-nrm * ph.x, -nrm * ph.y) : a;  // the new subdiagonal e_j
+      col[j + 1] = (beta != R(0)) ? mk<R>(-nrm * ph.x, -nrm * ph.y) : a;  // the new subdiagonal e_j
       s_v0[j] = v0;  // v_{j+1}; v_i for i >= j + 2 stay in col[i]
     }
     __syncthreads();
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(NT) heevk_kernel(EigArgs<R> g) {
     for (int i = 0; i + 1 < n; ++i) {
       R di = Ldd[(int64_t)i * k + t], li = Ldl[(int64_t)i * k + t];
       if (fabs(di) >= fabs(li)) {
-        if (di == R(0)) { di = pert; Ldd[(int64_t)i * k + t] = di; }
+        if (fabs(di) < pert) { di = (di < R(0)) ? -pert : pert; Ldd[(int64_t)i * k + t] = di; }
         R f = li / di;
         Ldl[(int64_t)i * k + t] = f;
         Ldd[(int64_t)(i + 1) * k + t] -= f * Ldu[(int64_t)i * k + t];
@@ -224,7 +224,10 @@ __global__ void __launch_bounds__(NT) heevk_kernel(EigArgs<R> g) {
         Lpiv[(int64_t)i * k + t] = 1;
       }
     }
-    if (Ldd[(int64_t)(n - 1) * k + t] == R(0)) Ldd[(int64_t)(n - 1) * k + t] = pert;
+    {
+      R dl_ = Ldd[(int64_t)(n - 1) * k + t];
+      if (fabs(dl_) < pert) Ldd[(int64_t)(n - 1) * k + t] = (dl_ < R(0)) ? -pert : pert;
+    }
     // start vector
     for (int i = 0; i < n; ++i) {
       uint32_t h = hash32((uint32_t)(t * 7919 + 1) * 2654435761u ^ (uint32_t)(i * 40503 + 17));

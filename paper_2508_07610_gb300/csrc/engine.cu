@@ -76,8 +76,38 @@ struct EngBase {
   // capture snapshot
   std::vector<int> snap_bond, snap_kraus, snap_slot;
   int snap_centre = 0;
+  // optional per-launch CUDA-event timing by kernel class (not while capturing)
+  enum { P_GEMM = 0, P_QR = 1, P_EIG = 2, P_OTHER = 3, P_N = 4 };
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev_pool;
+  struct Rec {
+    int cls;
+    int e0, e1;
+    double flops;
+  };
+  std::vector<Rec> recs;
+  int ev_next = 0;
+  int cur_cls = -1, cur_e0 = -1;
+  double cur_flops = 0;
+  void prof_start(int cls, double flops) {
+    if (!prof_on || capturing) return;
+    if (ev_next + 2 > (int)ev_pool.size()) return;
+    cur_cls = cls;
+    cur_flops = flops;
+    cur_e0 = ev_next++;
+    cudaEventRecord(ev_pool[cur_e0], stream);
+  }
+  void prof_stop() {
+    if (cur_cls < 0) return;
+    int e1 = ev_next++;
+    cudaEventRecord(ev_pool[e1], stream);
+    recs.push_back({cur_cls, cur_e0, e1, cur_flops});
+    cur_cls = -1;
+  }
 
-  virtual ~EngBase() {}
+  virtual ~EngBase() {
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+  }
   virtual mpdo_status alloc() = 0;
   virtual mpdo_status reset() = 0;
   virtual mpdo_status apply(int nq, int q, const double* Uhost, const double* Udev, const mpdo_chanset* ch,
@@ -234,7 +264,10 @@ struct Eng : EngBase {
     g.vb = vb;
     g.C = Cm;
     g.vc = vc;
-    CK(gemm<R>(stream, batch < 0 ? B : batch, g));
+    const int nb = batch < 0 ? B : batch;
+    prof_start(P_GEMM, 8.0 * M * N * K * nb);
+    CK(gemm<R>(stream, nb, g));
+    prof_stop();
     ++launches;
     return MPDO_OK;
   }
@@ -256,7 +289,9 @@ struct Eng : EngBase {
       a.disc = which >= 0 ? dDisc + which : nullptr;
       a.gap = which >= 0 ? dDisc + 2 : nullptr;
       a.disc_stride = 3;
+      prof_start(P_EIG, 8.0 * (16.0 / 3.0) * nmat * nmat * nmat * B);
       CK(heevk<ER>(stream, B, a));
+      prof_stop();
       ++launches;
     } else {
       // FP64 eigensolver on complex64 Gram matrices
@@ -275,7 +310,9 @@ struct Eng : EngBase {
       a.disc = which >= 0 ? dDisc + which : nullptr;
       a.gap = which >= 0 ? dDisc + 2 : nullptr;
       a.disc_stride = 3;
+      prof_start(P_EIG, 8.0 * (16.0 / 3.0) * nmat * nmat * nmat * B);
       CK(heevk<ER>(stream, B, a));
+      prof_stop();
       CK((convert<ER, R>(stream, sU * B, wU64, wU)));
       launches += 3;
     }
@@ -300,7 +337,9 @@ struct Eng : EngBase {
     a.qstride = sQR;
     a.qout = slot_ptr(sa);
     a.vq = row_major(x, slot_elems);
+    prof_start(P_QR, 8.0 * (4.0 * a.m * a.n * (double)(a.m < a.n ? a.m : a.n)) * B);
     CK(qr<R>(stream, B, a));
+    prof_stop();
     ++launches;
     // site c+1 <- R . A_{c+1}
     const int N = 2 * dn2 * dr2;
@@ -331,7 +370,9 @@ struct Eng : EngBase {
     a.qstride = sQR;
     a.qout = slot_ptr(sa);
     a.vq = v2(slot_elems, 0, 0, 1, 0, 0, L, 1);  // Q^H written as the new x x L site
+    prof_start(P_QR, 8.0 * (4.0 * a.m * a.n * (double)(a.m < a.n ? a.m : a.n)) * B);
     CK(qr<R>(stream, B, a));
+    prof_stop();
     ++launches;
     // site c-1 <- A_{c-1} . R^H
     const int M = dlp * 2 * dnp;
@@ -375,7 +416,9 @@ struct Eng : EngBase {
     f.Khat = wK;
     f.Rt = nq == 2 ? wRt : nullptr;
     // idx_dev == nullptr: one channel for all, or channel b for chain b (handled by chan_idx below)
+    prof_start(P_OTHER, 0);
     CK(fuse_gate<R>(stream, B, f));
+    prof_stop();
     ++launches;
     return MPDO_OK;
   }
@@ -415,7 +458,9 @@ struct Eng : EngBase {
   mpdo_status apply1(int q, int rk) {
     const int dl = bond[q], dn = kraus[q], dr = bond[q + 1];
     const int NK = rk * dn, S = 2 * dl;
+    prof_start(P_OTHER, 8.0 * 2 * NK * S * dr * B);
     CK(apply_1q_kraus<R>(stream, B, dl, dn, dr, rk, site_ptr(q), slot_elems, wK, wX, sX));
+    prof_stop();
     ++launches;
     const int kap = imin(kappa_max, imin(S * dr, NK));
     const int so = take_slot();
@@ -443,7 +488,9 @@ struct Eng : EngBase {
     qa.Qw = wQ;
     qa.qstride = sQR;
     qa.qout = nullptr;
+    prof_start(P_QR, 8.0 * (4.0 * qa.m * qa.n * (double)(qa.m < qa.n ? qa.m : qa.n)) * B);
     CK(qr<R>(stream, B, qa));
+    prof_stop();
     ++launches;
     const View R1 = col_major(m, sQR);
     // 2. E = A2 A2^H with A2 as (2dm) x (dn2 dr)
@@ -452,7 +499,9 @@ struct Eng : EngBase {
                            v2(slot_elems, 0, 0, 1, 0, 0, K2, 1), wE, row_major(C2, sE));
     if (st) return st;
     // 3. T[c][a][c'][b] from E and the reduced superoperator of the fused gate
+    prof_start(P_OTHER, 8.0 * 4 * 16 * dm * dm * B);
     CK(build_T<R>(stream, B, dm, wRt, wE, sE, wT, sT));
+    prof_stop();
     ++launches;
     // 4. Z[x][(a, c', b)] = sum_c R1[x, c] T[c][(a, c', b)]
     const int NZ = 4 * C2;
@@ -489,7 +538,9 @@ struct Eng : EngBase {
     st = gemm_(2 * kchi, C2, x, wU, v2(sU, 2, (int64_t)2 * x, 1, 0, 0, 2, 1), wQR, R1, wH, row_major(C2, sH));
     if (st) return st;
     // 9. Y[(b', p2', k)][(bb, p2)] = sum Khat_k[(p1' p2'), (p1 p2)] H[(b', p1')][(p1, bb)]
+    prof_start(P_OTHER, 8.0 * 4 * kchi * 2 * rk * C2 * B);
     CK(build_Y<R>(stream, B, kchi, dm, rk, wK, wH, sH, wY, sY));
+    prof_stop();
     ++launches;
     // 10. X (Kraus-major [(k, n2)][(b', p2')][r]) = Y . A2
     const int S = 2 * kchi, NK = rk * dn2;
@@ -1344,6 +1395,41 @@ mpdo_status mpdo_set_centre(mpdo_t h, int q) {
   if (h->e->capturing) return MPDO_ESTATE;
   if (q < 0 || q >= h->e->n) return MPDO_EINVAL;
   h->e->centre = q;
+  return MPDO_OK;
+}
+
+mpdo_status mpdo_profile(mpdo_t h, int enable) {
+  if (!h) return MPDO_EINVAL;
+  EngBase* e = h->e;
+  if (e->capturing) return MPDO_ESTATE;
+  if (enable && e->ev_pool.empty()) {
+    e->ev_pool.resize(1 << 16);
+    for (auto& ev : e->ev_pool)
+      if (cudaEventCreate(&ev) != cudaSuccess) return MPDO_ECUDA;
+  }
+  e->prof_on = enable != 0;
+  return MPDO_OK;
+}
+
+mpdo_status mpdo_profile_read(mpdo_t h, double* ms, double* flops, long long* count) {
+  if (!h || !ms || !flops || !count) return MPDO_EINVAL;
+  EngBase* e = h->e;
+  if (e->capturing) return MPDO_ESTATE;
+  if (cudaStreamSynchronize(e->stream) != cudaSuccess) return MPDO_ECUDA;
+  for (int c = 0; c < EngBase::P_N; ++c) {
+    ms[c] = 0;
+    flops[c] = 0;
+    count[c] = 0;
+  }
+  for (auto& r : e->recs) {
+    float t = 0;
+    if (cudaEventElapsedTime(&t, e->ev_pool[r.e0], e->ev_pool[r.e1]) != cudaSuccess) return MPDO_ECUDA;
+    ms[r.cls] += t;
+    flops[r.cls] += r.flops;
+    count[r.cls] += 1;
+  }
+  e->recs.clear();
+  e->ev_next = 0;
   return MPDO_OK;
 }
 

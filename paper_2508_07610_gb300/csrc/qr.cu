@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(NT) qr_kernel(QrArgs<R> g) {
     const R aa = sqrt(norm2(a));
     const R nrm = sqrt(aa * aa + s);
     cplx<R> ph = (aa > R(0)) ? mk<R>(a.x / aa, a.y / aa) : mk<R>(1, 0);
-    const R beta = (nrm > R(0)) ? R(1) / (nrm * (nrm + aa)) : R(0);
+    const R beta = (nrm > tiny_norm<R>()) ? R(1) / (nrm * (nrm + aa)) : R(0);
     const cplx<R> v0 = a + nrm * ph;
     if (tid == 0) {
       s_beta[j] = beta;
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(NT) qr_kernel(QrArgs<R> g) {
       }
     }
     __syncthreads();
-    if (tid == 0) col[j] = (nrm > R(0)) ? mk<R>(-nrm * ph.x, -nrm * ph.y) : a;
+    if (tid == 0) col[j] = (beta != R(0)) ? mk<R>(-nrm * ph.x, -nrm * ph.y) : a;
     __syncthreads();
   }
 

@@ -64,6 +64,8 @@ def lib():
         "mpdo_get_site": [vp, i32, i32, dp, ip],
         "mpdo_set_site": [vp, i32, i32, i32, i32, dp],
         "mpdo_set_centre": [vp, i32],
+        "mpdo_profile": [vp, i32],
+        "mpdo_profile_read": [vp, dp, dp, C.POINTER(C.c_longlong)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -173,6 +175,18 @@ class MPDO:
 
     def launch_count(self) -> int:
         return int(lib().mpdo_launch_count(self.h))
+
+    def profile(self, enable: bool = True):
+        _check(lib().mpdo_profile(self.h, 1 if enable else 0), "mpdo_profile")
+
+    def profile_read(self):
+        """{class: (ms, flops, launches)} for classes gemm, qr, eig, other."""
+        ms, fl = np.zeros(4), np.zeros(4)
+        cnt = np.zeros(4, dtype=np.int64)
+        _check(lib().mpdo_profile_read(self.h, ms.ctypes.data_as(C.POINTER(C.c_double)),
+                                       fl.ctypes.data_as(C.POINTER(C.c_double)),
+                                       cnt.ctypes.data_as(C.POINTER(C.c_longlong))), "mpdo_profile_read")
+        return {name: (float(ms[i]), float(fl[i]), int(cnt[i])) for i, name in enumerate(("gemm", "qr", "eig", "other"))}
 
     # -------------------------------------------------------------- channels and gates
     def channels(self, nq: int, chis, tol: float = 1e-12) -> ChannelSet:

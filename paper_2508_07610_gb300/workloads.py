@@ -372,3 +372,24 @@ def random_circuit(n: int, n_ops: int, rng, rank1: int = 3, rank2: int = 6, p2q:
             ch = _add_chan(chis, 1, random_channel_kraus(1, rank1, rng))
             ops.append(Op(1, q, random_unitary(2, rng), ch))
     return _circuit(n, ops, chis, {"name": f"random_n{n}_{n_ops}"})
+
+
+def random_right_canonical_sites(n: int, chi: int, kappa: int, rng, centre_scale: float = 1.0):
+    """A random MPDO state with every bond at its cap: site 0 is a random tensor of unit norm and
+    every other site is a random right isometry (its (l) x (p, n, r) matrix has orthonormal rows),
+    so the orthogonality centre is site 0.  Bonds are min(chi, 2*kappa*bond_left, ...) shaped like a
+    saturated chain; the Kraus legs all have dimension kappa."""
+    bonds = [1] * (n + 1)
+    for q in range(1, n):
+        bonds[q] = min(chi, (2 * kappa) ** min(q, n - q))
+    sites = []
+    for q in range(n):
+        dl, dr = bonds[q], bonds[q + 1]
+        if q == 0:
+            A = rng.normal(size=(dl, 2, kappa, dr)) + 1j * rng.normal(size=(dl, 2, kappa, dr))
+            A *= centre_scale / np.linalg.norm(A)
+        else:
+            U = random_unitary(2 * kappa * dr, rng)
+            A = U[:dl, :].reshape(dl, 2, kappa, dr)
+        sites.append(np.ascontiguousarray(A, dtype=np.complex128))
+    return sites
