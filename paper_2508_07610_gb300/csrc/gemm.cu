@@ -10,6 +10,23 @@ namespace {
 constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
 
 template <typename R>
+struct kCompensated {
+  static constexpr bool value = false;
+};
+template <>
+struct kCompensated<float> {
+  static constexpr bool value = true;
+};
+// s + c += x with Knuth's TwoSum: s takes the rounded sum, c collects the exact rounding error
+__device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
+  float t = __fadd_rn(s, x);
+  float bp = __fsub_rn(t, s);
+  float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+  s = t;
+  c = __fadd_rn(c, err);
+}
+
+template <typename R>
 __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs<R> g, int a_m_fast, int b_n_fast) {
   __shared__ cplx<R> As[BK][BM];
   __shared__ cplx<R> Bs[BK][BN];
@@ -38,9 +55,14 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs<R> g, int a_m_fast, i
     boff[t] = (j < g.N) ? view_col(g.vb, j) : -1;
   }
 
-  cplx<R> acc[4][4];
+  // acc holds the running sum; for FP32 each k-tile is summed into `part` first and added to
+  // (acc, comp) with an error-free TwoSum, so the rounding error no longer grows with K.
+  cplx<R> acc[4][4], comp[4][4];
   for (int r = 0; r < 4; ++r)
-    for (int c = 0; c < 4; ++c) acc[r][c] = mk<R>(0, 0);
+    for (int c = 0; c < 4; ++c) {
+      acc[r][c] = mk<R>(0, 0);
+      comp[r][c] = mk<R>(0, 0);
+    }
 
   for (int k0 = 0; k0 < g.K; k0 += BK) {
     for (int t = 0; t < 4; ++t) {
@@ -62,13 +84,32 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs<R> g, int a_m_fast, i
       Bs[bk[t]][bj[t]] = v;
     }
     __syncthreads();
-#pragma unroll 4
-    for (int kk = 0; kk < BK; ++kk) {
-      cplx<R> a[4], b[4];
-      for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + 16 * r];
-      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + 16 * c];
+    if constexpr (kCompensated<R>::value) {
+      cplx<R> part[4][4];
       for (int r = 0; r < 4; ++r)
-        for (int c = 0; c < 4; ++c) cfma(acc[r][c], a[r], b[c]);
+        for (int c = 0; c < 4; ++c) part[r][c] = mk<R>(0, 0);
+#pragma unroll 4
+      for (int kk = 0; kk < BK; ++kk) {
+        cplx<R> a[4], b[4];
+        for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + 16 * r];
+        for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + 16 * c];
+        for (int r = 0; r < 4; ++r)
+          for (int c = 0; c < 4; ++c) cfma(part[r][c], a[r], b[c]);
+      }
+      for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) {
+          two_sum_acc(acc[r][c].x, comp[r][c].x, part[r][c].x);
+          two_sum_acc(acc[r][c].y, comp[r][c].y, part[r][c].y);
+        }
+    } else {
+#pragma unroll 4
+      for (int kk = 0; kk < BK; ++kk) {
+        cplx<R> a[4], b[4];
+        for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + 16 * r];
+        for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + 16 * c];
+        for (int r = 0; r < 4; ++r)
+          for (int c = 0; c < 4; ++c) cfma(acc[r][c], a[r], b[c]);
+      }
     }
     __syncthreads();
   }
@@ -82,7 +123,7 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs<R> g, int a_m_fast, i
       int j = n0 + tx + 16 * c;
       if (j >= g.N) continue;
       int64_t o = ro + view_col(g.vc, j);
-      cplx<R> v = g.alpha * acc[r][c];
+      cplx<R> v = g.alpha * (acc[r][c] + comp[r][c]);
       if (use_beta) {
         cplx<R> old = C[o];
         if (g.vc.conj) old.y = -old.y;

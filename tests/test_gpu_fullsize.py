@@ -1,0 +1,81 @@
+"""Parity at the benchmark's full size (n = 20, chi_max = 64, kappa_max = 8, two-qubit channel of
+Kraus rank 16), where the CPU reference can only afford single updates.
+
+A seeded random right-canonical chain with every bond at 64 and every Kraus leg at 8 is loaded into
+both implementations; one noisy CZ update is applied; the discarded weights and the reduced density
+matrix of the two touched qubits (a gauge-invariant output; with the centre on the pair it needs no
+environment) are compared element by element.  A second test runs whole ansatz layers at full size
+in the complex64 mode and in FP64 on the GPU and compares every <Z_i Z_j>.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import channels as OC
+from oracle import mpdo as OM
+from paper_2508_07610_gb300 import mpdo as G
+from paper_2508_07610_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+N, CHI, KAP = 20, 64, 8
+
+
+def _pair_rdm(A1, A2):
+    """rho[(p1 p2), (p1' p2')] of two adjacent sites whose environments are identities."""
+    th = np.einsum("lanb,bcmr->lacnmr", A1, A2)  # [l, p1, p2, n1, n2, r]
+    m = th.reshape(th.shape[0], 4, -1, th.shape[-1])
+    return np.einsum("lxkr,lykr->xy", m, m.conj())
+
+
+def _state(seed):
+    rng = np.random.default_rng(seed)
+    return W.random_right_canonical_sites(N, CHI, KAP, rng)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-6)])
+def test_single_update_full_size(prec, tol):
+    sites = _state(2026)
+    chi2 = W.kraus_to_chi(W.compose(W.depolarizing_2q(1e-2), W.unitary_channel(W.zz_phase(0.013))))
+    q = 9
+    orc = OM.MPDO(N, CHI, KAP)
+    orc.sites = [s.copy() for s in sites]
+    orc.centre = 0
+    orc.apply_2q(q, W.cz(), OC.chi_to_kraus(chi2, 2))
+
+    st = G.MPDO(N, CHI, KAP, prec)
+    for i, s in enumerate(sites):
+        st.set_site(i, s)
+    st.set_centre(0)
+    ch = st.channels(2, [chi2])
+    st.apply_2q(q, W.cz(), ch)
+    st.sync()
+
+    d = st.discarded()[0]
+    assert abs(d[0] - orc.discarded_chi) < tol, (d[0], orc.discarded_chi)
+    assert abs(d[1] - orc.discarded_kappa) < tol, (d[1], orc.discarded_kappa)
+    bg, kg = st.dims()
+    assert bg == orc.bond_dims() and kg == orc.kraus_dims()
+    r_g = _pair_rdm(st.get_site(q), st.get_site(q + 1))
+    r_o = _pair_rdm(orc.sites[q], orc.sites[q + 1])
+    scale = np.trace(r_o).real
+    err = np.max(np.abs(r_g - r_o)) / scale
+    print(f"full-size single update {prec}: rdm err {err:.2e}, discarded {d[0]:.3e} / {d[1]:.3e}")
+    assert err < tol
+    zz = st.zz(q, q + 1)[0]
+    assert abs(zz - orc.expect_zz(q, q + 1)) < tol
+
+
+def test_complex64_layers_track_fp64_at_full_size():
+    """Six ansatz layers of the benchmark workload (n = 20, chi = 64, kappa = 8) in MIXED and FP64."""
+    circ = W.hea(n=N, depth=6, seed=W.MASTER_SEED + 2)
+    zz = {}
+    for prec in ("fp64", "mixed"):
+        st = G.run_circuit(circ, CHI, KAP, prec)
+        zz[prec] = st.zz_map()[0]
+        bonds, _ = st.dims()
+        assert max(bonds) == CHI
+    err = float(np.max(np.abs(zz["mixed"] - zz["fp64"])))
+    print(f"n=20 chi=64 kappa=8, 6 layers: max |ZZ_mixed - ZZ_fp64| = {err:.2e}")
+    assert err < 1e-6
