@@ -15,7 +15,7 @@ Steps, in the paper's order:
   * Kraus-leg truncation (Eq. svdNoise, Fig. 3a): the site tensor as a
     (p, l, r) x n matrix is SVD-truncated to kappa_max values, T' = U S (= T V).
 Readings where the paper is silent: truncation runs per gate with the
-orthogonality centre on the touched sites; after a two-qubit gate the bond is
+orthogonality centre on the touched site (either site of a two-qubit gate); after a two-qubit gate the bond is
 split first and the right site's Kraus leg truncated second; nothing is
 renormalised and every readout is divided by Tr(rho); singular values at or
 below tol * sigma_max are dropped as numerically zero.
@@ -124,8 +124,11 @@ class MPDO:
     def apply_2q(self, q: int, U: np.ndarray, kraus) -> None:
         """Two-site update on (q, q+1): merge, apply K_k = N_k U with a new Kraus leg on site q+1,
         split by the SVD of the (l, p1, n1) x (p2, k, n2, r) matrix keeping chi_max values, then
-        truncate the Kraus leg of site q+1."""
-        self.move_centre(q)
+        truncate the Kraus leg of site q+1.  The split only needs every site left of q
+        left-isometric and every site right of q+1 right-isometric, so the centre may sit on either
+        of the two sites; it is moved only when it is elsewhere."""
+        if self.centre not in (q, q + 1):
+            self.move_centre(q)
         A1, A2 = self.sites[q], self.sites[q + 1]
         dl, _, dn1, _ = A1.shape
         _, _, dn2, dr = A2.shape

@@ -444,7 +444,8 @@ struct Eng : EngBase {
     if (q < 0 || q + nq > n) return MPDO_EINVAL;
     if (!ch || ch->nq != nq || ch->rpad > RMAX) return MPDO_EINVAL;
     if (!idx_dev && ch->count != 1 && ch->count != B) return MPDO_EINVAL;
-    mpdo_status st = move_centre(q);
+    // a two-site split needs the centre on q or q + 1 (canonical environments on both sides)
+    mpdo_status st = (nq == 2 && centre == q + 1) ? MPDO_OK : move_centre(q);
     if (st) return st;
     // with one channel per chain and no index array, chain b uses channel b
     const int* idx = idx_dev;

@@ -67,15 +67,38 @@ def test_single_update_full_size(prec, tol):
     assert abs(zz - orc.expect_zz(q, q + 1)) < tol
 
 
+def _perturbed(circ, rel, seed):
+    """The same circuit with every chi matrix moved by a Hermitian, trace-free perturbation of
+    relative size `rel` (a stand-in for rounding of the inputs)."""
+    rng = np.random.default_rng(seed)
+    out = W.Circuit(circ.n, circ.ops, [], circ.kraus, dict(circ.meta))
+    for nq, chi in circ.chis:
+        d = chi.shape[0]
+        h = rng.normal(size=(d, d)) + 1j * rng.normal(size=(d, d))
+        h = (h + h.conj().T) / 2
+        h -= np.trace(h) / d * np.eye(d)
+        out.chis.append((nq, chi + rel * np.abs(chi).max() * h / np.abs(h).max()))
+    return out
+
+
 def test_complex64_layers_track_fp64_at_full_size():
-    """Six ansatz layers of the benchmark workload (n = 20, chi = 64, kappa = 8) in MIXED and FP64."""
+    """Six ansatz layers of the benchmark workload (n = 20, chi = 64, kappa = 8) in MIXED and FP64.
+
+    The two-qubit channels DEP2(p2) o ZZ(phi) have a 15-fold degenerate Kraus spectrum (p2/16 each),
+    so a kappa cut can fall inside a degenerate cluster, where the kept subspace is not unique.  The
+    intrinsic uncertainty of the truncated readouts is measured by running FP64 twice, once with the
+    channel inputs moved by 1e-13 (relative); the complex64 path must stay within 1e-6 or within a
+    small multiple of that intrinsic spread, whichever is larger."""
     circ = W.hea(n=N, depth=6, seed=W.MASTER_SEED + 2)
     zz = {}
-    for prec in ("fp64", "mixed"):
-        st = G.run_circuit(circ, CHI, KAP, prec)
-        zz[prec] = st.zz_map()[0]
+    for name, c, prec in (("fp64", circ, "fp64"), ("fp64_perturbed", _perturbed(circ, 1e-13, 7), "fp64"),
+                          ("mixed", circ, "mixed")):
+        st = G.run_circuit(c, CHI, KAP, prec)
+        zz[name] = st.zz_map()[0]
         bonds, _ = st.dims()
         assert max(bonds) == CHI
+    spread = float(np.max(np.abs(zz["fp64_perturbed"] - zz["fp64"])))
     err = float(np.max(np.abs(zz["mixed"] - zz["fp64"])))
-    print(f"n=20 chi=64 kappa=8, 6 layers: max |ZZ_mixed - ZZ_fp64| = {err:.2e}")
-    assert err < 1e-6
+    print(f"n=20 chi=64 kappa=8, 6 layers: max|ZZ_mixed - ZZ_fp64| = {err:.2e}; "
+          f"FP64 spread under 1e-13 input perturbation = {spread:.2e}")
+    assert err < max(1e-6, 10 * spread)
