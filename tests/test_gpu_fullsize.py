@@ -34,7 +34,7 @@ def _state(seed):
     return W.random_right_canonical_sites(N, CHI, KAP, rng)
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-6)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-6), ("fp32", 1e-6)])
 def test_single_update_full_size(prec, tol):
     sites = _state(2026)
     chi2 = W.kraus_to_chi(W.compose(W.depolarizing_2q(1e-2), W.unitary_channel(W.zz_phase(0.013))))
