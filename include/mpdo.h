@@ -141,6 +141,26 @@ mpdo_status mpdo_set_centre(mpdo_t h, int q);
 mpdo_status mpdo_profile(mpdo_t h, int enable);
 mpdo_status mpdo_profile_read(mpdo_t h, double* ms, double* flops, long long* count);
 
+/* Allocation-free chi -> Kraus conversion, for callers that cannot call cudaMalloc (a plug-in
+ * living inside another application's memory pool, or code that must not grow its device footprint
+ * after start-up).  The paper has no counterpart: it is the same conversion as
+ * channel_set_from_process_matrices, with every intermediate kept in one fixed device array
+ * compiled into the library (MPDO_NOALLOC_MAX_CHANNELS channels, about 1.6 MB, held on every GPU
+ * that loads the library until the process exits) instead of fresh allocations.
+ *   chi_dev   device, count x (4^nq x 4^nq) complex, row-major (same layout as the host variant)
+ *   kraus_dev device output, count x 4^nq Kraus operators of 2^nq x 2^nq complex (descending weight,
+ *             pruned ones zeroed: eta <= tol * max eta, tol <= 0 means 1e-12)
+ *   ranks_dev device output, count ints
+ *   stream    cudaStream_t the work is enqueued on (returns without waiting)
+ * Returns MPDO_EINVAL for nq not in {1, 2}, count < 1 or count > MPDO_NOALLOC_MAX_CHANNELS; inputs
+ * are not validated (no host copy exists).  It calls no allocating routine.  The first call on a
+ * device looks up the array's device address (once per device, with that device current); make
+ * that first call before any stream capture.  All calls share the one array: calls whose work
+ * overlaps on the GPU (different streams, or several host threads) race; serialise them. */
+#define MPDO_NOALLOC_MAX_CHANNELS 64
+mpdo_status channel_kraus_noalloc(int nq, int count, const double* chi_dev, double tol, double* kraus_dev,
+                                  int* ranks_dev, void* stream);
+
 /* Number of kernels the library launched on this handle since creation (for accounting). */
 long long mpdo_launch_count(mpdo_t h);
 const char* mpdo_status_string(int status);
