@@ -95,12 +95,10 @@ def depolarizing_1q(p: float) -> List[np.ndarray]:
 
 def depolarizing_2q(p: float) -> List[np.ndarray]:
     """(1-p) rho + p I/4: sqrt(1-15p/16) II and sqrt(p/16) for the 15 other Pauli pairs."""
-    out = []
-    for a in range(4):
-        for b in range(4):
-            w = 1 - 15 * p / 16 if (a == 0 and b == 0) else p / 16
-            out.append(math.sqrt(w) * np.kron(PAULIS[a], PAULIS[b]))
-    return out
+    pauli_strings(2)
+    w = np.full(16, math.sqrt(p / 16))
+    w[0] = math.sqrt(1 - 15 * p / 16)
+    return list(w[:, None, None] * _PAULI_CACHE[2])
 
 
 def amplitude_damping(g: float) -> List[np.ndarray]:
@@ -114,15 +112,21 @@ def unitary_channel(U: np.ndarray) -> List[np.ndarray]:
 
 
 def compose(second: Sequence[np.ndarray], first: Sequence[np.ndarray]) -> List[np.ndarray]:
-    """Kraus set of `second` applied after `first`."""
-    return [B @ A for A in first for B in second]
+    """Kraus set of `second` applied after `first` (ordered first-major)."""
+    prod = np.einsum("bij,ajk->abik", np.asarray(second), np.asarray(first))
+    return list(prod.reshape(-1, prod.shape[-2], prod.shape[-1]))
+
+
+_PAULI_CACHE = {}
 
 
 def pauli_strings(nq: int) -> List[np.ndarray]:
-    out = [np.ones((1, 1), dtype=np.complex128)]
-    for _ in range(nq):
-        out = [np.kron(o, P) for o in out for P in PAULIS]
-    return out
+    if nq not in _PAULI_CACHE:
+        out = [np.ones((1, 1), dtype=np.complex128)]
+        for _ in range(nq):
+            out = [np.kron(o, P) for o in out for P in PAULIS]
+        _PAULI_CACHE[nq] = np.stack(out)
+    return list(_PAULI_CACHE[nq])
 
 
 def kraus_to_chi(kraus: Sequence[np.ndarray]) -> np.ndarray:
@@ -131,10 +135,12 @@ def kraus_to_chi(kraus: Sequence[np.ndarray]) -> np.ndarray:
     Writing K_k = sum_m c_km sigma_m (c_km = Tr(sigma_m K_k) / d) gives
     eps(rho) = sum_mn (sum_k c_km conj(c_kn)) sigma_m rho sigma_n^dagger.
     """
-    d = kraus[0].shape[0]
+    K = np.asarray(kraus, dtype=np.complex128)
+    d = K.shape[-1]
     nq = int(round(math.log2(d)))
-    basis = pauli_strings(nq)
-    c = np.array([[np.trace(P.conj().T @ K) / d for P in basis] for K in kraus])
+    pauli_strings(nq)
+    P = _PAULI_CACHE[nq]
+    c = np.einsum("mij,kij->km", P.conj(), K) / d  # Tr(sigma_m^dagger K_k) / d (Paulis are Hermitian)
     return c.T @ c.conj()
 
 
