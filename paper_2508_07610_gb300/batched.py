@@ -5,7 +5,7 @@ Circuits whose gates sit on the same positions in the same order (same qubit cou
 chains at once, each chain with its own gate matrix and its own channel (per-chain channel sets,
 uploaded once).  Each group's whole circuit is captured into one CUDA graph (reset included), so a
 replay runs the full circuit on the GPU without host involvement.  Different groups are
-independent and run one after another on the same stream.
+independent and run concurrently, each group on its own CUDA stream.
 """
 from __future__ import annotations
 
@@ -60,7 +60,7 @@ class BatchedRun:
     """All circuits of a workload, grouped by gate-position signature."""
 
     def __init__(self, circuits: Sequence, chi_max: int, kappa_max: int, prec="mixed", stream: int = 0,
-                 torch=None):
+                 torch=None, concurrent: bool = True):
         if torch is None:
             import torch as _t
             torch = _t
@@ -71,8 +71,13 @@ class BatchedRun:
             sig = (c.n, tuple((o.kind, o.q) for o in c.ops))
             by_sig.setdefault(sig, []).append(i)
         self.groups: List[Group] = []
+        self.streams = []
         for sig, idx in by_sig.items():
-            self.groups.append(Group([self.circuits[i] for i in idx], idx, chi_max, kappa_max, prec, stream, torch))
+            s = stream
+            if concurrent:
+                self.streams.append(torch.cuda.Stream())
+                s = self.streams[-1].cuda_stream
+            self.groups.append(Group([self.circuits[i] for i in idx], idx, chi_max, kappa_max, prec, s, torch))
 
     def run(self, graphs: bool = True):
         for g in self.groups:
