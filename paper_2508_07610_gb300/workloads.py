@@ -206,18 +206,26 @@ def ghz_ansatz(n: int = 6, depth: int = 3, seed: int = MASTER_SEED + 1) -> Circu
     return _circuit(n, ops, chis, {"name": f"ghz_ansatz_n{n}_d{depth}"})
 
 
-def hea_channels(n: int, rng) -> Tuple[list, list, list]:
-    """Per-qubit 1q channels AD(g) o DEP(p1) and per-pair 2q channels DEP2(p2) o ZZ(phi)."""
+def hea_channels(n: int, rng, scale: float = 1.0, record: dict = None) -> Tuple[list, list, list]:
+    """Per-qubit 1q channels AD(g) o DEP(p1) and per-pair 2q channels DEP2(p2) o ZZ(phi), with
+    p1 ~ U(5e-4, 2e-3), g ~ U(1e-3, 4e-3), p2 ~ U(5e-3, 2e-2), phi ~ N(0, 0.01), all strengths
+    multiplied by `scale`; the drawn values are appended to `record` when one is given."""
     chis = _Chans()
     c1 = []
     for _ in range(n):
-        p1 = rng.uniform(5e-4, 2e-3)
-        g = rng.uniform(1e-3, 4e-3)
+        p1 = scale * rng.uniform(5e-4, 2e-3)
+        g = scale * rng.uniform(1e-3, 4e-3)
+        if record is not None:
+            record.setdefault("p1", []).append(p1)
+            record.setdefault("gamma", []).append(g)
         c1.append(_add_chan(chis, 1, compose(amplitude_damping(g), depolarizing_1q(p1))))
     c2 = []
     for _ in range(n - 1):
-        p2 = rng.uniform(5e-3, 2e-2)
-        phi = rng.normal(0.0, 0.01)
+        p2 = scale * rng.uniform(5e-3, 2e-2)
+        phi = scale * rng.normal(0.0, 0.01)
+        if record is not None:
+            record.setdefault("p2", []).append(p2)
+            record.setdefault("phi", []).append(phi)
         c2.append(_add_chan(chis, 2, compose(depolarizing_2q(p2), unitary_channel(zz_phase(phi)))))
     return chis, c1, c2
 
@@ -261,17 +269,19 @@ def random_regular3(n: int, rng) -> List[Tuple[int, int]]:
             return sorted(edges)
 
 
-def qaoa_maxcut(n: int, p: int, edges, gammas, betas, rng, chis=None, c1=None, c2=None, cswap=None) -> Circuit:
+def qaoa_maxcut(n: int, p: int, edges, gammas, betas, rng, chis=None, c1=None, c2=None, cswap=None,
+                scale: float = 1.0) -> Circuit:
     """Noisy QAOA for MaxCut on a 1D chain: H layer, then per layer a full odd-even
     transposition SWAP network (n rounds) in which every adjacent pair that is a graph edge
     receives the cost gate fused with its SWAP, followed by the mixer on every qubit.
     meta['perm'][i] is the logical vertex sitting at chain position i at the end."""
+    record = {}
     if chis is None:
-        chis, c1, c2 = hea_channels(n, rng)
+        chis, c1, c2 = hea_channels(n, rng, scale, record)
         cswap = []
         for q in range(n - 1):
-            p2 = rng.uniform(5e-3, 2e-2)
-            phi = rng.normal(0.0, 0.01)
+            p2 = scale * rng.uniform(5e-3, 2e-2)
+            phi = scale * rng.normal(0.0, 0.01)
             cswap.append(_add_chan(chis, 2, compose(depolarizing_2q(2 * p2), unitary_channel(zz_phase(phi)))))
     eset = set((min(a, b), max(a, b)) for a, b in edges)
     ops = [Op(1, q, hadamard(), c1[q]) for q in range(n)]
@@ -301,7 +311,7 @@ def qaoa_maxcut(n: int, p: int, edges, gammas, betas, rng, chis=None, c1=None, c
         for q in range(n):
             ops.append(Op(1, q, qaoa_mixer(b), c1[q]))
     return _circuit(n, ops, chis, {"name": f"qaoa_n{n}_p{p}", "edges": sorted(eset), "perm": pos,
-                                   "gammas": list(gammas), "betas": list(betas)})
+                                   "gammas": list(gammas), "betas": list(betas), "noise": record})
 
 
 def qaoa_batch(count: int, seed: int = MASTER_SEED + 3, n_choices=tuple(range(8, 25, 2)), p_max: int = 4):
@@ -399,3 +409,19 @@ def random_right_canonical_sites(n: int, chi: int, kappa: int, rng, centre_scale
             A = U[:dl, :].reshape(dl, 2, kappa, dr)
         sites.append(np.ascontiguousarray(A, dtype=np.complex128))
     return sites
+
+
+def surrogate_features(circ, p_max: int = 4) -> np.ndarray:
+    """16 inputs of the screening surrogate: gamma_1..4 and beta_1..4 (zero-padded to p_max = 4,
+    divided by pi) and the means and spreads of p1, p2, gamma, phi over the chain (divided by the
+    middle of their ranges)."""
+    g = np.zeros(p_max)
+    b = np.zeros(p_max)
+    gm, bt = circ.meta["gammas"], circ.meta["betas"]
+    g[:len(gm)] = np.asarray(gm) / math.pi
+    b[:len(bt)] = np.asarray(bt) / math.pi
+    rec = circ.meta["noise"]
+    ref = {"p1": 1.25e-3, "p2": 1.25e-2, "gamma": 2.5e-3, "phi": 1e-2}
+    means = [np.mean(rec[k]) / ref[k] for k in ("p1", "p2", "gamma", "phi")]
+    spreads = [np.std(rec[k]) / ref[k] for k in ("p1", "p2", "gamma", "phi")]
+    return np.concatenate([g, b, means, spreads]).astype(np.float32)
