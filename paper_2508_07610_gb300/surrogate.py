@@ -173,14 +173,15 @@ def screen(model: Surrogate, candidates, chi, kappa, prec, torch, top: int = 64,
            X: Optional[np.ndarray] = None):
     """Rank candidates by predicted <H_MaxCut>/|E|, re-score the top ones with the MPDO, and fall back
     to the MPDO alone (the first `top` candidates in their given order) when the surrogate's error on
-    the re-scored set exceeds tol.  Returns (best index, its MPDO score, surrogate error, fell back)."""
+    the re-scored set (root-mean-square over it) exceeds tol.  Returns (best index, its MPDO score,
+    surrogate error, fell back)."""
     if X is None:
         X = features(candidates)
     Xd = torch.tensor(X, device="cuda")
     pred = model.forward(Xd)[:, 0].cpu().numpy()
     order = np.argsort(-pred)[:top]
     scored = mpdo_targets([candidates[i] for i in order], chi, kappa, prec, torch)[:, 0]
-    err = float(np.max(np.abs(scored - pred[order])))
+    err = float(np.sqrt(np.mean((scored - pred[order]) ** 2)))
     if err > tol:
         order = np.arange(min(top, len(candidates)))
         scored = mpdo_targets([candidates[i] for i in order], chi, kappa, prec, torch)[:, 0]
