@@ -57,14 +57,15 @@ def test_training_fits_a_smooth_function(torch):
 
 
 def test_screened_loop_beats_the_loop_without_the_surrogate(torch):
-    """Train on MPDO-generated samples of noisy QAOA on one fixed 8-vertex 3-regular graph, then with the
+    """Train on MPDO-generated samples of noisy p = 1 QAOA on one fixed 8-vertex 3-regular graph (angles
+    and noise strength varied), then with the
     same MPDO budget (64 re-scored candidates) the surrogate-screened search must find a better
     <H_MaxCut> than scoring 64 unscreened candidates."""
     rng = np.random.default_rng(W.MASTER_SEED + 5)
     n = 8
     edges = W.random_regular3(n, rng)
     chi, kap, prec = 16, 4, "mixed"
-    train = S.sample_circuits(4096, n, edges, rng, p_choices=(1, 2))
+    train = S.sample_circuits(4096, n, edges, rng, p_choices=(1,))
     Y = S.mpdo_targets(train, chi, kap, prec, torch)
     X = S.features(train)
     model = S.Surrogate(torch, max_batch=4096, seed=11)
@@ -72,19 +73,19 @@ def test_screened_loop_beats_the_loop_without_the_surrogate(torch):
     losses = model.train(Xd, Yd, epochs=400, batch=256, lr=2e-3)
     assert losses[-1] < 0.1 * losses[0]
     # held-out error of the surrogate
-    test = S.sample_circuits(256, n, edges, rng, p_choices=(1, 2))
+    test = S.sample_circuits(256, n, edges, rng, p_choices=(1,))
     Yt = S.mpdo_targets(test, chi, kap, prec, torch)
     pt = model.forward(torch.tensor(S.features(test), device="cuda")).cpu().numpy()
     rmse = float(np.sqrt(np.mean((pt[:, 0] - Yt[:, 0]) ** 2)))
     print(f"surrogate held-out RMSE of <H_MaxCut>/|E|: {rmse:.4f}, final training loss {losses[-1]:.2e}")
     assert rmse < 0.05
-    # screening: candidates at one noise setting, p = 2
+    # screening: candidates at one noise setting, p = 1
     cand = []
     crng = np.random.default_rng(99)
     for _ in range(2048):
-        g = crng.uniform(0, math.pi, size=2)
-        b = crng.uniform(0, math.pi, size=2)
-        cand.append(W.qaoa_maxcut(n, 2, edges, g, b, np.random.default_rng(7), scale=1.0))
+        g = crng.uniform(0, math.pi, size=1)
+        b = crng.uniform(0, math.pi, size=1)
+        cand.append(W.qaoa_maxcut(n, 1, edges, g, b, np.random.default_rng(7), scale=1.0))
     best_i, best_screened, err, fell_back = S.screen(model, cand, chi, kap, prec, torch, top=64, tol=0.05)
     unscreened = S.mpdo_targets(cand[:64], chi, kap, prec, torch)[:, 0]
     print(f"screened best {best_screened:.4f} (surrogate error {err:.3f}, fallback {fell_back}) "
