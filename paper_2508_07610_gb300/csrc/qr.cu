@@ -6,7 +6,11 @@
 // in the column-major work matrix W (ld = m) and writes the thin Q (m x x, orthonormal columns)
 // both to the column-major buffer Qw (ld = m) and, when given, through an output View.
 // Reflectors are H = I - beta v v^H with v = y + e^{i arg y0} |y| e_0, so H y = -e^{i arg y0} |y| e_0.
+#include <cooperative_groups.h>
+
 #include "kernels.h"
+
+namespace cg = cooperative_groups;
 
 namespace mpdo {
 
@@ -126,6 +130,199 @@ __global__ void __launch_bounds__(NT) qr_kernel(QrArgs<R> g) {
     }
   }
 }
+// ---------------------------------------------------------------------------------------------
+// Cluster variant: the C CTAs of a thread-block cluster hold the m x n matrix in their shared memory,
+// ceil(m / C) rows each, so every pass over the trailing matrix runs from on-chip memory.  Column
+// norms and the reflector-column dot products are reduced across the cluster through distributed
+// shared memory (two alternating partial buffers, one cluster barrier per reduction).  Q is formed in
+// place after R has been written out.  Every loop has a fixed trip count shared by the whole cluster.
+template <typename R>
+__global__ void __launch_bounds__(NT) qr_cluster_kernel(QrArgs<R> g, int C, int mloc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int z = blockIdx.x / C;
+  const int m = g.m, n = g.n, x = (m < n) ? m : n;
+  const int r0 = rank * mloc;
+  const int r1 = (r0 + mloc < m) ? r0 + mloc : m;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  cplx<R>* Wl = reinterpret_cast<cplx<R>*>(smem_raw);        // [n][mloc] column-major
+  cplx<R>* red = Wl + (int64_t)mloc * n;                       // 2 x (n + 2) partials
+  cplx<R>* wv = red + 2 * (n + 2);                              // n gathered values
+  cplx<R>* s_v0 = wv + n;                                       // n
+  R* s_beta = reinterpret_cast<R*>(s_v0 + n);                   // n
+  R* bred = s_beta + n;                                         // NT / 32
+  cplx<R>* W = g.W + (int64_t)z * g.wstride;
+  cplx<R>* Qg = g.Qw + (int64_t)z * g.qstride;
+  const cplx<R>* in = g.in + view_batch(g.vin, z);
+
+  for (int64_t e = tid; e < (int64_t)mloc * n; e += NT) {
+    int il = (int)(e % mloc), j = (int)(e / mloc);
+    int i = r0 + il;
+    cplx<R> v = mk<R>(0, 0);
+    if (i < r1) {
+      v = in[view_row(g.vin, i) + view_col(g.vin, j)];
+      if (g.vin.conj) v.y = -v.y;
+    }
+    Wl[e] = v;
+  }
+  __syncthreads();
+
+  int buf = 0;
+  // gather slot `slot` (count values) of buffer `b` from every CTA into wv, summed in rank order
+  auto gather = [&](int b, int count) {
+    for (int c = tid; c < count; c += NT) {
+      cplx<R> acc = mk<R>(0, 0);
+      for (int r = 0; r < C; ++r) {
+        cplx<R>* rem = cluster.map_shared_rank(red + b * (n + 2), r);
+        acc = acc + rem[c];
+      }
+      wv[c] = acc;
+    }
+    __syncthreads();
+  };
+
+  for (int j = 0; j < x; ++j) {
+    const cplx<R>* col = Wl + (int64_t)j * mloc;
+    // partial |column j below j|^2 and the diagonal entry (from its owner)
+    R s = 0;
+    for (int i = (j + 1 > r0 ? j + 1 : r0) + tid; i < r1; i += NT) s += norm2(col[i - r0]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) bred[wid] = s;
+    __syncthreads();
+    if (tid == 0) {
+      R t = 0;
+      for (int w = 0; w < NT / 32; ++w) t += bred[w];
+      red[buf * (n + 2) + 0] = mk<R>(t, 0);
+      red[buf * (n + 2) + 1] = (j >= r0 && j < r1) ? col[j - r0] : mk<R>(0, 0);
+    }
+    cluster.sync();
+    gather(buf, 2);
+    buf ^= 1;
+    const cplx<R> a = wv[1];
+    const R aa = sqrt(norm2(a));
+    const R nrm = sqrt(aa * aa + wv[0].x);
+    const cplx<R> ph = (aa > R(0)) ? mk<R>(a.x / aa, a.y / aa) : mk<R>(1, 0);
+    const R beta = (nrm > tiny_norm<R>()) ? R(1) / (nrm * (nrm + aa)) : R(0);
+    const cplx<R> v0 = a + nrm * ph;
+    if (beta != R(0)) {
+      // partial w_c = v^H W[:, c] over my rows, one warp per column
+      for (int c = j + 1 + wid; c < n; c += NT / 32) {
+        const cplx<R>* y = Wl + (int64_t)c * mloc;
+        cplx<R> acc = mk<R>(0, 0);
+        if (lane == 0 && j >= r0 && j < r1) cfma_cj(acc, v0, y[j - r0]);
+        for (int i = (j + 1 > r0 ? j + 1 : r0) + lane; i < r1; i += 32) cfma_cj(acc, col[i - r0], y[i - r0]);
+        acc = warp_csum(acc);
+        if (lane == 0) red[buf * (n + 2) + c] = acc;
+      }
+    }
+    cluster.sync();  // taken whether or not beta vanished, so every CTA passes the same barriers
+    if (beta != R(0)) {
+      for (int c = tid; c < n; c += NT) {
+        cplx<R> acc = mk<R>(0, 0);
+        if (c > j)
+          for (int r = 0; r < C; ++r) acc = acc + cluster.map_shared_rank(red + buf * (n + 2), r)[c];
+        wv[c] = beta * acc;
+      }
+      __syncthreads();
+      for (int64_t e = tid; e < (int64_t)(n - j - 1) * mloc; e += NT) {
+        int il = (int)(e % mloc), c = j + 1 + (int)(e / mloc);
+        int i = r0 + il;
+        if (i < j || i >= r1) continue;
+        cplx<R> vi = (i == j) ? v0 : col[il];
+        Wl[(int64_t)c * mloc + il] = Wl[(int64_t)c * mloc + il] - vi * wv[c];
+      }
+    }
+    buf ^= 1;
+    __syncthreads();
+    if (tid == 0) {
+      s_beta[j] = beta;
+      s_v0[j] = v0;
+      if (j >= r0 && j < r1) Wl[(int64_t)j * mloc + (j - r0)] = (beta != R(0)) ? mk<R>(-nrm * ph.x, -nrm * ph.y) : a;
+    }
+    __syncthreads();
+  }
+
+  // R (leading x rows, zeros below the diagonal) to the global work matrix
+  for (int64_t e = tid; e < (int64_t)mloc * n; e += NT) {
+    int il = (int)(e % mloc), c = (int)(e / mloc);
+    int i = r0 + il;
+    if (i < r1 && i < x) W[(int64_t)c * m + i] = (c >= i) ? Wl[e] : mk<R>(0, 0);
+  }
+  __syncthreads();
+  // Q in place: clear the strict upper triangle of the leading x columns, then apply the reflectors
+  for (int64_t e = tid; e < (int64_t)mloc * x; e += NT) {
+    int il = (int)(e % mloc), c = (int)(e / mloc);
+    if (r0 + il < c) Wl[e] = mk<R>(0, 0);
+  }
+  __syncthreads();
+  for (int j = x - 1; j >= 0; --j) {
+    const R beta = s_beta[j];
+    const cplx<R> v0 = s_v0[j];
+    const cplx<R>* col = Wl + (int64_t)j * mloc;
+    if (beta != R(0)) {
+      for (int c = j + 1 + wid; c < x; c += NT / 32) {
+        const cplx<R>* y = Wl + (int64_t)c * mloc;
+        cplx<R> acc = mk<R>(0, 0);
+        if (lane == 0 && j >= r0 && j < r1) cfma_cj(acc, v0, y[j - r0]);
+        for (int i = (j + 1 > r0 ? j + 1 : r0) + lane; i < r1; i += 32) cfma_cj(acc, col[i - r0], y[i - r0]);
+        acc = warp_csum(acc);
+        if (lane == 0) red[buf * (n + 2) + c] = acc;
+      }
+    }
+    cluster.sync();
+    if (beta != R(0)) {
+      for (int c = tid; c < x; c += NT) {
+        cplx<R> acc = mk<R>(0, 0);
+        if (c > j)
+          for (int r = 0; r < C; ++r) acc = acc + cluster.map_shared_rank(red + buf * (n + 2), r)[c];
+        wv[c] = beta * acc;
+      }
+      __syncthreads();
+      for (int64_t e = tid; e < (int64_t)(x - j - 1) * mloc; e += NT) {
+        int il = (int)(e % mloc), c = j + 1 + (int)(e / mloc);
+        int i = r0 + il;
+        if (i < j || i >= r1) continue;
+        cplx<R> vi = (i == j) ? v0 : col[il];
+        Wl[(int64_t)c * mloc + il] = Wl[(int64_t)c * mloc + il] - vi * wv[c];
+      }
+      __syncthreads();
+    }
+    // column j of Q: e_j - beta v conj(v0) on rows >= j, zero above
+    for (int il = tid; il < mloc; il += NT) {
+      int i = r0 + il;
+      if (i >= r1) continue;
+      cplx<R> q = mk<R>(0, 0);
+      if (i >= j) {
+        cplx<R> vi = (i == j) ? v0 : Wl[(int64_t)j * mloc + il];
+        q = mk<R>(i == j ? R(1) : R(0), R(0)) - beta * (vi * conjg(v0));
+      }
+      Wl[(int64_t)j * mloc + il] = q;
+    }
+    buf ^= 1;
+    __syncthreads();
+  }
+  // Q out: the column-major work buffer and, when given, the output view
+  cplx<R>* out = g.qout ? g.qout + view_batch(g.vq, z) : nullptr;
+  for (int64_t e = tid; e < (int64_t)mloc * x; e += NT) {
+    int il = (int)(e % mloc), c = (int)(e / mloc);
+    int i = r0 + il;
+    if (i >= r1) continue;
+    cplx<R> v = Wl[e];
+    Qg[(int64_t)c * m + i] = v;
+    if (out) {
+      if (g.vq.conj) v.y = -v.y;
+      out[view_row(g.vq, i) + view_col(g.vq, c)] = v;
+    }
+  }
+  cluster.sync();  // no CTA leaves while a peer may still read its shared memory
+}
+
+template <typename R>
+size_t cluster_smem_bytes(int mloc, int n) {
+  return sizeof(cplx<R>) * ((size_t)mloc * n + 2 * (n + 2) + 2 * (size_t)n) + sizeof(R) * ((size_t)n + NT / 32) + 64;
+}
+constexpr size_t kClusterSmemBudget = 200 * 1024;
 }  // namespace
 
 template <typename R>
@@ -133,6 +330,34 @@ cudaError_t qr(cudaStream_t s, int batch, const QrArgs<R>& g) {
   if (batch <= 0 || g.m <= 0 || g.n <= 0) return cudaSuccess;
   int x = g.m < g.n ? g.m : g.n;
   if (x > MAXX) return cudaErrorInvalidValue;
+  // smallest cluster (2, 4 or 8 CTAs) whose shared memory holds the matrix; otherwise the global kernel
+  for (int C = 2; C <= 8; C *= 2) {
+    int mloc = (g.m + C - 1) / C;
+    size_t bytes = cluster_smem_bytes<R>(mloc, g.n);
+    if (bytes > kClusterSmemBudget || g.m < 2 * C) continue;
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaError_t e = cudaFuncSetAttribute(qr_cluster_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)kClusterSmemBudget);
+      if (e != cudaSuccess) return e;
+      attr_set = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(batch * C));
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = bytes;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, qr_cluster_kernel<R>, g, C, mloc);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+  }
   qr_kernel<R><<<batch, NT, 0, s>>>(g);
   return cudaGetLastError();
 }
