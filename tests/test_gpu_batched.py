@@ -30,8 +30,10 @@ def test_batched_qaoa_matches_oracle(prec, tol, eps):
         ref, o = _oracle_maxcut(c, chi, kap)
         lim = tol + 4 * o.cut_sensitivity(eps) * len(c.meta["edges"])
         assert abs(mc[i] - ref) < lim, (i, mc[i], ref, lim)
-        assert abs(disc[i, 0] - o.discarded_chi) < max(tol, 1e-9)
-        assert abs(disc[i, 1] - o.discarded_kappa) < max(tol, 1e-9)
+        # cumulative over every truncation of the circuit: complex64 rounding of each term adds up
+        dtol = 1e-9 if prec == "fp64" else 2e-5
+        assert abs(disc[i, 0] - o.discarded_chi) < dtol
+        assert abs(disc[i, 1] - o.discarded_kappa) < dtol
     # replaying the graphs reproduces the result exactly
     run.run(graphs=True)
     assert np.array_equal(run.maxcut(), mc)

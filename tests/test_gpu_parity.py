@@ -45,7 +45,8 @@ def _check_state(st, orc, prec, n, chain=0, dense=True, label=""):
     for k, v in errs.items():
         lim = (tol_rho if k in ("rho", "trace") else tol_r) + sens
         if k.startswith("disc"):
-            lim = max(lim, 1e-9)
+            # cumulative over every truncation: complex64 rounding of each term adds up
+            lim = 1e-9 if prec == "fp64" else 2e-5
         assert v < lim, (k, v, lim)
 
 
