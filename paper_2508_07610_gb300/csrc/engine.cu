@@ -251,8 +251,10 @@ struct Eng : EngBase {
   std::vector<int> slots() const override { return site_slot; }
 
   // ---------------------------------------------------------------- kernels wrappers
-  mpdo_status gemm_(int M, int N, int K, const C* A, View va, const C* Bm, View vb, C* Cm, View vc, int batch = -1) {
+  mpdo_status gemm_(int M, int N, int K, const C* A, View va, const C* Bm, View vb, C* Cm, View vc, int batch = -1,
+                    int herm = 0) {
     GemmArgs<R> g;
+    g.herm = herm;
     g.M = M;
     g.N = N;
     g.K = K;
@@ -265,7 +267,12 @@ struct Eng : EngBase {
     g.C = Cm;
     g.vc = vc;
     const int nb = batch < 0 ? B : batch;
-    prof_start(P_GEMM, 8.0 * M * N * K * nb);
+    double frac = 1.0;  // a Hermitian result computes only the tiles on and below the diagonal
+    if (herm) {
+      double T = (M + 63) / 64;
+      frac = (T * (T + 1) / 2) / (T * T);
+    }
+    prof_start(P_GEMM, 8.0 * M * N * K * nb * frac);
     CK(gemm<R>(stream, nb, g));
     prof_stop();
     ++launches;
@@ -427,10 +434,14 @@ struct Eng : EngBase {
   // [l][p][nu][r] with S = dl*2 rows (l, p).  Eq. (svdNoise) through the Gram matrix X^* X^T.
   mpdo_status kappa_truncate_X(int NK, int S, int dr, int kap, int out_slot) {
     const int64_t L = (int64_t)S * dr;
-    // G = conj(X) X^T  (NK x NK, column-major)
+    // G = conj(X) X^T  (NK x NK, column-major, Hermitian: lower triangle computed, upper mirrored)
     mpdo_status st = gemm_(NK, NK, (int)L, wX, v2(sX, 0, 0, L, 0, 0, 1, 1), wX, v2(sX, 0, 0, 1, 0, 0, L, 0), wF,
-                           col_major(NK, sF));
+                           col_major(NK, sF), -1, 1);
     if (st) return st;
+    prof_start(P_OTHER, 0);
+    CK(herm_fill_upper<R>(stream, B, NK, wF, sF));
+    prof_stop();
+    ++launches;
     st = eig_(NK, kap, 1);
     if (st) return st;
     // A[(s, nu, r)] = sum_nk V[nk, nu] X[nk][s][r]

@@ -17,6 +17,7 @@ struct GemmArgs {
   View vb;  // K x N
   cplx<R>* C;
   View vc;  // M x N; vc.conj stores conj(result)
+  int herm = 0;  // M == N and the result is Hermitian: only tiles on or below the diagonal are computed
 };
 template <typename R>
 cudaError_t gemm(cudaStream_t s, int batch, const GemmArgs<R>& g);
@@ -111,6 +112,9 @@ cudaError_t dot_batch(cudaStream_t s, int batch, int64_t len, const cplx<R>* a, 
                       int64_t bstride, cplx<double>* out);
 template <typename R>
 cudaError_t fill(cudaStream_t s, int64_t count, cplx<R>* x, cplx<R> v);
+// complete a column-major Hermitian n x n matrix from its lower triangle: A[i, j] = conj(A[j, i]), i < j
+template <typename R>
+cudaError_t herm_fill_upper(cudaStream_t s, int batch, int n, cplx<R>* A, int64_t stride);
 // discarded-weight accumulators [batch][3] = (0, 0, +inf-like gap)
 cudaError_t init_discarded(cudaStream_t s, int batch, double* d);
 // generic permutation of a dense row-major tensor with up to 6 dims (batched)

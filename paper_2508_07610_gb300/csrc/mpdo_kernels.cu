@@ -262,6 +262,16 @@ __global__ void fill_kernel(int64_t count, cplx<R>* x, cplx<R> v) {
     x[e] = v;
 }
 
+template <typename R>
+__global__ void herm_fill_kernel(int n, cplx<R>* A, int64_t stride) {
+  cplx<R>* M = A + (int64_t)blockIdx.y * stride;
+  const int64_t total = (int64_t)n * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(e % n), j = (int)(e / n);
+    if (i < j) M[e] = conjg(M[(int64_t)i * n + j]);
+  }
+}
+
 __global__ void init_disc_kernel(int batch, double* d) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= batch) return;
@@ -311,6 +321,16 @@ cudaError_t choi_to_kraus(cudaStream_t s, int count, int nq, int rmax, const int
   choi_to_kraus_kernel<<<count, NT, 0, s>>>(count, nq, rmax, r_dev, eta, vecs, kraus);
   return cudaGetLastError();
 }
+template <typename R>
+cudaError_t herm_fill_upper(cudaStream_t s, int batch, int n, cplx<R>* A, int64_t stride) {
+  if (batch <= 0 || n <= 1) return cudaSuccess;
+  dim3 grid(grid_for((int64_t)n * n), batch);
+  herm_fill_kernel<R><<<grid, NT, 0, s>>>(n, A, stride);
+  return cudaGetLastError();
+}
+template cudaError_t herm_fill_upper<float>(cudaStream_t, int, int, cplx<float>*, int64_t);
+template cudaError_t herm_fill_upper<double>(cudaStream_t, int, int, cplx<double>*, int64_t);
+
 cudaError_t init_discarded(cudaStream_t s, int batch, double* d) {
   if (batch <= 0) return cudaSuccess;
   init_disc_kernel<<<(batch + 127) / 128, 128, 0, s>>>(batch, d);

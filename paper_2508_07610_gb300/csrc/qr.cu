@@ -330,11 +330,20 @@ cudaError_t qr(cudaStream_t s, int batch, const QrArgs<R>& g) {
   if (batch <= 0 || g.m <= 0 || g.n <= 0) return cudaSuccess;
   int x = g.m < g.n ? g.m : g.n;
   if (x > MAXX) return cudaErrorInvalidValue;
-  // smallest cluster (2, 4 or 8 CTAs) whose shared memory holds the matrix; otherwise the global kernel
+  // Few matrices (latency-bound): the smallest cluster (2, 4 or 8 CTAs) whose shared memory holds the
+  // matrix.  Many matrices (throughput-bound): one CTA per matrix, which keeps every SM busy with
+  // several small-footprint CTAs and spends fewer SM-cycles per factorisation.
+  static int n_sm = 0;
+  if (n_sm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0) n_sm = 1;
+  }
   for (int C = 2; C <= 8; C *= 2) {
     int mloc = (g.m + C - 1) / C;
     size_t bytes = cluster_smem_bytes<R>(mloc, g.n);
     if (bytes > kClusterSmemBudget || g.m < 2 * C) continue;
+    if ((int64_t)batch * C > n_sm) break;
     static bool attr_set = false;
     if (!attr_set) {
       cudaError_t e = cudaFuncSetAttribute(qr_cluster_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
