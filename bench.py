@@ -131,15 +131,31 @@ class Runner:
         return len(range(layer % 2, N_QUBITS - 1, 2))
 
     def layer(self, layer, U1=None):
-        """One ansatz layer in a single left-to-right sweep (gates on disjoint qubits commute)."""
+        """One ansatz layer as a sweep (gates on disjoint qubits commute, so only the per-qubit order
+        matters): even layers (bonds 0-1, 2-3, ...) left to right, odd layers (bonds 1-2, ..., 17-18)
+        right to left.  In each pair the 1q gate on the far site truncates its Kraus leg through the
+        centre's environment, so the centre moves once per pair (twice in the leftward sweep)."""
         st = self.st
         U1 = self.U1 if U1 is None else U1
         li = layer % self.depth
-        par = layer % 2
-        for q in range(N_QUBITS):
+
+        def one(q, neighbour):
+            st.set_neighbour_truncation(neighbour)
             st.apply_1q_batch(q, U1[li, q].data_ptr(), self.ch1[q])
-            if q >= 1 and (q - 1) % 2 == par and q - 1 < N_QUBITS - 1:
-                st.apply_2q_batch(q - 1, self.CZ.data_ptr(), self.ch2[q - 1])
+
+        if layer % 2 == 0:  # N_QUBITS is even: bonds 0-1, ..., 18-19 cover every qubit
+            for q in range(0, N_QUBITS - 1, 2):
+                one(q, False)
+                one(q + 1, True)
+                st.apply_2q_batch(q, self.CZ.data_ptr(), self.ch2[q])
+        else:  # bonds 1-2, ..., 17-18; qubits 19 and 0 have no partner
+            one(N_QUBITS - 1, False)
+            for q in range(N_QUBITS - 3, 0, -2):
+                one(q + 1, False)
+                one(q, True)
+                st.apply_2q_batch(q, self.CZ.data_ptr(), self.ch2[q])
+            one(0, False)
+        st.set_neighbour_truncation(False)
 
 
 def run_ours(args, torch, rank, world):

@@ -133,6 +133,16 @@ mpdo_status mpdo_get_site(mpdo_t h, int chain, int q, double* out, int* dims);
 mpdo_status mpdo_set_site(mpdo_t h, int q, int dl, int dn, int dr, const double* data);
 mpdo_status mpdo_set_centre(mpdo_t h, int q);
 
+/* When enabled, a noisy 1q gate on a site next to the orthogonality centre truncates its Kraus leg
+ * through the centre's environment (the Gram of the centre over the shared bond) instead of first
+ * moving the centre there with a QR step.  The kept subspace is the same as with the move (the
+ * ancilla density of the site is the same matrix), so results agree up to rounding; the site is left
+ * non-isometric until the next operation absorbs it (a two-qubit gate on that pair, or a centre move,
+ * which then starts by moving onto it).  Useful for a sweep order in which the gate on the far site of
+ * a pair is followed by the two-qubit gate on the pair.  Off by default; capturable (the setting is
+ * read when each call is made). */
+mpdo_status mpdo_set_neighbour_truncation(mpdo_t h, int enable);
+
 /* Per-launch CUDA-event timing by kernel class (0 GEMM, 1 QR, 2 eigensolver, 3 other), for
  * measurement: enable records an event pair around every launch made outside graph capture;
  * read synchronises and returns, per class, the summed milliseconds, the summed algorithmic

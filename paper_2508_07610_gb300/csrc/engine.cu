@@ -73,6 +73,10 @@ struct EngBase {
   std::vector<int> bond;   // n + 1 entries, bond[0] = bond[n] = 1
   std::vector<int> kraus;  // n entries
   int centre = 0;
+  // A site next to the centre whose Kraus leg was truncated through the centre's environment (so it
+  // is not isometric); -1 when every site other than the centre is isometric.
+  int dirty = -1;
+  bool neighbour_trunc = false;  // let 1q gates on a neighbour of the centre skip the centre move
   // capture snapshot
   std::vector<int> snap_bond, snap_kraus, snap_slot;
   int snap_centre = 0;
@@ -116,6 +120,7 @@ struct EngBase {
   virtual mpdo_status expect(int kind, const int* args, int nargs, double* out) = 0;
   virtual mpdo_status restore_layout() = 0;
   virtual std::vector<int> slots() const = 0;
+  virtual mpdo_status clean() = 0;
   virtual mpdo_status save(FILE* f) = 0;
   virtual mpdo_status get_site(int chain, int q, double* out) = 0;
   virtual mpdo_status set_site(int q, int dl, int dn, int dr, const double* data) = 0;
@@ -199,7 +204,7 @@ struct Eng : EngBase {
     CK(dmalloc(&wU, sU * B));
     sH = 4 * X * X;
     CK(dmalloc(&wH, sH * B));
-    sY = 4 * X * X * RMAX;
+    sY = lmax(4 * X * X * RMAX, 8 * K * X * X);
     CK(dmalloc(&wY, sY * B));
     sX = 2 * RMAX * K * X * X;
     CK(dmalloc(&wX, sX * B));
@@ -249,6 +254,11 @@ struct Eng : EngBase {
   }
 
   std::vector<int> slots() const override { return site_slot; }
+  // make every site other than the centre isometric again (absorbs a non-isometric neighbour)
+  mpdo_status clean() override {
+    if (dirty < 0) return MPDO_OK;
+    return move_centre(dirty);
+  }
 
   // ---------------------------------------------------------------- kernels wrappers
   mpdo_status gemm_(int M, int N, int K, const C* A, View va, const C* Bm, View vb, C* Cm, View vc, int batch = -1,
@@ -394,6 +404,13 @@ struct Eng : EngBase {
     return MPDO_OK;
   }
   mpdo_status move_centre(int q) {
+    // the first hop goes onto a non-isometric neighbour, which makes it the centre again
+    if (dirty >= 0 && dirty != centre) {
+      mpdo_status s = (dirty == centre + 1) ? shift_right(centre) : shift_left(centre);
+      if (s) return s;
+      centre = dirty;
+    }
+    dirty = -1;
     while (centre < q) {
       mpdo_status s = shift_right(centre);
       if (s) return s;
@@ -432,11 +449,13 @@ struct Eng : EngBase {
 
   // Kraus-leg truncation of a tensor held Kraus-major in wX: X[nk][s][r] (NK x S*dr) -> new site
   // [l][p][nu][r] with S = dl*2 rows (l, p).  Eq. (svdNoise) through the Gram matrix X^* X^T.
-  mpdo_status kappa_truncate_X(int NK, int S, int dr, int kap, int out_slot) {
+  // With Yg (same layout as X, stride sY) the Gram is conj(X) Yg^T: Yg carries the environment of a
+  // site next to the centre.
+  mpdo_status kappa_truncate_X(int NK, int S, int dr, int kap, int out_slot, const C* Yg = nullptr) {
     const int64_t L = (int64_t)S * dr;
     // G = conj(X) X^T  (NK x NK, column-major, Hermitian: lower triangle computed, upper mirrored)
-    mpdo_status st = gemm_(NK, NK, (int)L, wX, v2(sX, 0, 0, L, 0, 0, 1, 1), wX, v2(sX, 0, 0, 1, 0, 0, L, 0), wF,
-                           col_major(NK, sF), -1, 1);
+    mpdo_status st = gemm_(NK, NK, (int)L, wX, v2(sX, 0, 0, L, 0, 0, 1, 1), Yg ? Yg : wX,
+                           v2(Yg ? sY : sX, 0, 0, 1, 0, 0, L, 0), wF, col_major(NK, sF), -1, 1);
     if (st) return st;
     prof_start(P_OTHER, 0);
     CK(herm_fill_upper<R>(stream, B, NK, wF, sF));
@@ -455,15 +474,77 @@ struct Eng : EngBase {
     if (q < 0 || q + nq > n) return MPDO_EINVAL;
     if (!ch || ch->nq != nq || ch->rpad > RMAX) return MPDO_EINVAL;
     if (!idx_dev && ch->count != 1 && ch->count != B) return MPDO_EINVAL;
-    // a two-site split needs the centre on q or q + 1 (canonical environments on both sides)
-    mpdo_status st = (nq == 2 && centre == q + 1) ? MPDO_OK : move_centre(q);
+    // a two-site split needs the centre on q or q + 1 (canonical environments on both sides); the other
+    // site of the pair may be the non-isometric neighbour
+    bool env = false;
+    mpdo_status st = MPDO_OK;
+    if (nq == 2) {
+      bool in_pair = (centre == q || centre == q + 1) && (dirty < 0 || dirty == q || dirty == q + 1);
+      if (!in_pair) st = move_centre(q);
+    } else if (centre != q) {
+      env = neighbour_trunc && (q == centre + 1 || q == centre - 1) && (dirty < 0 || dirty == q);
+      if (!env) st = move_centre(q);
+    }
     if (st) return st;
     // with one channel per chain and no index array, chain b uses channel b
     const int* idx = idx_dev;
     if (!idx && ch->count == B && B > 1) idx = iota;
     st = fuse_(nq, Uhost, Udev, ch, idx);
     if (st) return st;
-    return nq == 1 ? apply1(q, ch->rpad) : apply2(q, ch->rpad);
+    if (nq == 2) {
+      st = apply2(q, ch->rpad);
+      dirty = -1;
+      return st;
+    }
+    return env ? apply1_neighbour(q, ch->rpad) : apply1(q, ch->rpad);
+  }
+
+  // Noisy 1q gate on a neighbour s of the centre c without moving the centre.  The Kraus-leg Gram of
+  // s is its exact ancilla density: with every other site isometric, the sites beyond s contribute an
+  // identity and the centre contributes its Gram over the shared bond, L (s = c + 1) or E (s = c - 1).
+  // The kept subspace is therefore the one a centre move would have produced.
+  mpdo_status apply1_neighbour(int q, int rk) {
+    const int c = centre;
+    const int dl = bond[q], dn = kraus[q], dr = bond[q + 1];
+    const int NK = rk * dn, S = 2 * dl;
+    const int64_t Lx = (int64_t)S * dr;
+    const C* Ac = site_ptr(c);
+    mpdo_status st;
+    if (q == c + 1) {
+      // L[b, b'] = sum_(l,p,n) conj(Ac[(lpn), b]) Ac[(lpn), b'],  b over bond q (= dl)
+      const int K = bond[c] * 2 * kraus[c];
+      st = gemm_(dl, dl, K, Ac, v2(slot_elems, 0, 0, 1, 0, 0, dl, 1), Ac, row_major(dl, slot_elems), wE,
+                 row_major(dl, sE));
+      if (st) return st;
+    } else {
+      // E[b, b'] = sum_(p,n,r) conj(Ac[b, (pnr)]) Ac[b', (pnr)],  b over bond c (= dr)
+      const int K = 2 * kraus[c] * bond[c + 1];
+      st = gemm_(dr, dr, K, Ac, v2(slot_elems, 0, 0, K, 0, 0, 1, 1), Ac, v2(slot_elems, 0, 0, 1, 0, 0, K), wE,
+                 row_major(dr, sE));
+      if (st) return st;
+    }
+    prof_start(P_OTHER, 8.0 * 2 * NK * S * dr * B);
+    CK(apply_1q_kraus<R>(stream, B, dl, dn, dr, rk, site_ptr(q), slot_elems, wK, wX, sX));
+    prof_stop();
+    ++launches;
+    if (q == c + 1) {
+      // Y[nk][b][(p r)] = sum_b' L[b, b'] X[nk][b'][(p r)]
+      st = gemm_(dl, (int)(NK * 2 * dr), dl, wE, row_major(dl, sE), wX, v2(sX, 0, 0, 2 * dr, 2 * dr, Lx, 1), wY,
+                 v2(sY, 0, 0, 2 * dr, 2 * dr, Lx, 1));
+    } else {
+      // Y[(nk l p)][b] = sum_b' X[(nk l p)][b'] E[b, b']
+      st = gemm_(NK * S, dr, dr, wX, row_major(dr, sX), wE, v2(sE, 0, 0, 1, 0, 0, dr), wY, row_major(dr, sY));
+    }
+    if (st) return st;
+    const int kap = imin(kappa_max, imin((int)Lx, NK));
+    const int so = take_slot();
+    st = kappa_truncate_X(NK, S, dr, kap, so, wY);
+    if (st) return st;
+    give_slot(site_slot[q]);
+    site_slot[q] = so;
+    kraus[q] = kap;
+    dirty = q;
+    return MPDO_OK;
   }
   int* iota = nullptr;  // device [0, 1, ..., B-1]
 
@@ -1282,6 +1363,8 @@ mpdo_status mpdo_save(mpdo_t h, const char* path) {
   EngBase* e = h->e;
   if (e->capturing) return MPDO_ESTATE;
   // canonical layout: centre first to 0 is not needed; store dims and centre as they are
+  mpdo_status cst = e->clean();
+  if (cst) return cst;
   FILE* f = fopen(path, "wb");
   if (!f) return MPDO_EINVAL;
   int hdr[6] = {e->B, e->n, e->chi_max, e->kappa_max, e->prec, e->centre};
@@ -1328,6 +1411,8 @@ mpdo_status mpdo_capture_begin(mpdo_t h) {
   EngBase* e = h->e;
   if (e->capturing) return MPDO_ESTATE;
   if (e->stream == nullptr) return MPDO_ESTATE;  // the legacy stream cannot be captured
+  mpdo_status cst = e->clean();
+  if (cst) return cst;
   if (cudaStreamSynchronize(e->stream) != cudaSuccess) return MPDO_ECUDA;
   e->snap_bond = e->bond;
   e->snap_kraus = e->kraus;
@@ -1407,6 +1492,13 @@ mpdo_status mpdo_set_centre(mpdo_t h, int q) {
   if (h->e->capturing) return MPDO_ESTATE;
   if (q < 0 || q >= h->e->n) return MPDO_EINVAL;
   h->e->centre = q;
+  h->e->dirty = -1;
+  return MPDO_OK;
+}
+
+mpdo_status mpdo_set_neighbour_truncation(mpdo_t h, int enable) {
+  if (!h) return MPDO_EINVAL;
+  h->e->neighbour_trunc = enable != 0;
   return MPDO_OK;
 }
 

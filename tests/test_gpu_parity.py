@@ -251,3 +251,56 @@ def test_graph_capture_replays_circuit():
         st.sync()
         assert np.max(np.abs(st.zz_map() - ref.zz_map())) < 1e-13
         assert np.max(np.abs(st.discarded() - ref.discarded())) < 1e-14
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_neighbour_truncation_matches_centre_moves(seed):
+    """With neighbour truncation on, 1q gates next to the centre truncate through the centre's
+    environment; the oracle moves the centre.  The states must agree."""
+    rng = np.random.default_rng(500 + seed)
+    n = 6
+    circ = W.random_circuit(n, 40, rng, rank1=4, rank2=6, p2q=0.4)
+    st = G.MPDO(n, 6, 3, "fp64")
+    st.set_neighbour_truncation(True)
+    chans = {}
+    for op in circ.ops:
+        ch = chans.get(op.chan)
+        if ch is None:
+            ch = chans[op.chan] = st.channels(op.kind, [circ.chis[op.chan][1]])
+        (st.apply_1q if op.kind == 1 else st.apply_2q)(op.q, op.U, ch)
+    orc = OM.run_circuit(circ, 6, 3)
+    _check_state(st, orc, "fp64", n, label=f"neighbour truncation seed {seed}")
+
+
+def test_neighbour_truncation_layer_pattern():
+    """The benchmark's sweep pattern (pairs left to right, then right to left, far site through the
+    centre) on a 7-qubit chain, against the oracle."""
+    rng = np.random.default_rng(31)
+    n = 7
+    st = G.MPDO(n, 8, 4, "fp64")
+    orc = OM.MPDO(n, 8, 4)
+    keep = []
+
+    def gate(kind, q, neighbour):
+        U = W.random_unitary(2 ** kind, rng)
+        chi = W.kraus_to_chi(W.random_channel_kraus(kind, 3 if kind == 1 else 5, rng))
+        ch = st.channels(kind, [chi])
+        keep.append(ch)
+        st.set_neighbour_truncation(neighbour)
+        (st.apply_1q if kind == 1 else st.apply_2q)(q, U, ch)
+        (orc.apply_1q if kind == 1 else orc.apply_2q)(q, U, OC.chi_to_kraus(chi, kind))
+
+    for layer in range(4):
+        if layer % 2 == 0:
+            for q in range(0, n - 1, 2):
+                gate(1, q, False)
+                gate(1, q + 1, True)
+                gate(2, q, False)
+            gate(1, n - 1, False)
+        else:
+            for q in range(n - 2, 0, -2):
+                gate(1, q + 1, False)
+                gate(1, q, True)
+                gate(2, q, False)
+            gate(1, 0, False)
+    _check_state(st, orc, "fp64", n, label="neighbour layer pattern")
