@@ -279,7 +279,8 @@ struct Eng : EngBase {
     const int nb = batch < 0 ? B : batch;
     double frac = 1.0;  // a Hermitian result computes only the tiles on and below the diagonal
     if (herm) {
-      double T = (M + 63) / 64;
+      const int tile = (M <= 32 && N <= 32) ? 32 : 64;
+      double T = (M + tile - 1) / tile;
       frac = (T * (T + 1) / 2) / (T * T);
     }
     prof_start(P_GEMM, 8.0 * M * N * K * nb * frac);

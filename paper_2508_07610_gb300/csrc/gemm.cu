@@ -184,12 +184,15 @@ template <typename R>
 cudaError_t gemm(cudaStream_t s, int batch, const GemmArgs<R>& g) {
   if (batch <= 0 || g.M <= 0 || g.N <= 0) return cudaSuccess;
   if (g.herm && g.M != g.N) return cudaErrorInvalidValue;
+  // small outputs (<= 32 x 32 per batch item: the Kraus-leg Gram of a 1q gate, the rank-kappa
+  // projection) take 32 x 32 tiles so that no tile is mostly padding
+  const bool small = g.M <= 32 && g.N <= 32;
   if constexpr (sizeof(R) == 4) {
-    if (g.K >= 1024) return launch<R, true, 4, 4>(s, batch, g);
+    if (g.K >= 1024) return small ? launch<R, true, 2, 2>(s, batch, g) : launch<R, true, 4, 4>(s, batch, g);
     if (g.M > 64 && !g.herm) return launch<R, false, 8, 4>(s, batch, g);
-    return launch<R, false, 4, 4>(s, batch, g);
+    return small ? launch<R, false, 2, 2>(s, batch, g) : launch<R, false, 4, 4>(s, batch, g);
   } else {
-    return launch<R, false, 4, 4>(s, batch, g);
+    return small ? launch<R, false, 2, 2>(s, batch, g) : launch<R, false, 4, 4>(s, batch, g);
   }
 }
 
