@@ -171,6 +171,11 @@ mpdo_status mpdo_profile_read(mpdo_t h, double* ms, double* flops, long long* co
 mpdo_status channel_kraus_noalloc(int nq, int count, const double* chi_dev, double tol, double* kraus_dev,
                                   int* ranks_dev, void* stream);
 
+/* Diagnostic: multiplies random complex64 M x K and K x N matrices with the tensor-core GEMM (tcgen05,
+ * TF32 split into hi + lo parts, FP32 accumulation) and with the CUDA-core GEMM, and returns the
+ * largest entry-wise difference relative to the largest entry, and the kernel's wait-timeout flag. */
+mpdo_status mpdo_tc_selftest(int M, int N, int K, double* max_rel_err, int* err_flag);
+
 /* Number of kernels the library launched on this handle since creation (for accounting). */
 long long mpdo_launch_count(mpdo_t h);
 const char* mpdo_status_string(int status);

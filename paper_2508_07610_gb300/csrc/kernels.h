@@ -22,6 +22,11 @@ struct GemmArgs {
 template <typename R>
 cudaError_t gemm(cudaStream_t s, int batch, const GemmArgs<R>& g);
 
+// tensor-core (tcgen05, split TF32) complex64 GEMM; applicable to non-Hermitian M >= 128 products
+bool tc_gemm_applicable(const GemmArgs<float>& g);
+cudaError_t tc_gemm(cudaStream_t s, int batch, const GemmArgs<float>& g);
+int tc_gemm_error_flag();
+
 template <typename R>
 struct QrArgs {
   int m, n;
