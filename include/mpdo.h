@@ -171,6 +171,12 @@ mpdo_status mpdo_profile_read(mpdo_t h, double* ms, double* flops, long long* co
 mpdo_status channel_kraus_noalloc(int nq, int count, const double* chi_dev, double tol, double* kraus_dev,
                                   int* ranks_dev, void* stream);
 
+/* In the complex64 modes, products with at least 128 rows and 64 columns, an inner dimension of at
+ * most 2048 and a non-Hermitian result run on the tensor cores (tcgen05.mma, each FP32 operand split
+ * into two TF32 parts, three TF32 products per real product, FP32 accumulation); the others, and
+ * every product when this is off, run on the CUDA cores.  On by default; no effect in MPDO_FP64. */
+mpdo_status mpdo_set_tensor_cores(mpdo_t h, int enable);
+
 /* Diagnostic: multiplies random complex64 M x K and K x N matrices with the tensor-core GEMM (tcgen05,
  * TF32 split into hi + lo parts, FP32 accumulation) and with the CUDA-core GEMM, and returns the
  * largest entry-wise difference relative to the largest entry, and the kernel's wait-timeout flag. */

@@ -77,6 +77,7 @@ struct EngBase {
   // is not isometric); -1 when every site other than the centre is isometric.
   int dirty = -1;
   bool neighbour_trunc = false;  // let 1q gates on a neighbour of the centre skip the centre move
+  bool tensor_cores = true;      // complex64 products that qualify run on the tcgen05 GEMM
   // capture snapshot
   std::vector<int> snap_bond, snap_kraus, snap_slot;
   int snap_centre = 0;
@@ -265,6 +266,7 @@ struct Eng : EngBase {
                     int herm = 0) {
     GemmArgs<R> g;
     g.herm = herm;
+    g.allow_tc = tensor_cores ? 1 : 0;
     g.M = M;
     g.N = N;
     g.K = K;
@@ -1494,6 +1496,12 @@ mpdo_status mpdo_set_centre(mpdo_t h, int q) {
   if (q < 0 || q >= h->e->n) return MPDO_EINVAL;
   h->e->centre = q;
   h->e->dirty = -1;
+  return MPDO_OK;
+}
+
+mpdo_status mpdo_set_tensor_cores(mpdo_t h, int enable) {
+  if (!h) return MPDO_EINVAL;
+  h->e->tensor_cores = enable != 0;
   return MPDO_OK;
 }
 

@@ -188,6 +188,7 @@ cudaError_t gemm(cudaStream_t s, int batch, const GemmArgs<R>& g) {
   // projection) take 32 x 32 tiles so that no tile is mostly padding
   const bool small = g.M <= 32 && g.N <= 32;
   if constexpr (sizeof(R) == 4) {
+    if (g.allow_tc && g.K <= 2048 && tc_gemm_applicable(g)) return tc_gemm(s, batch, g);
     if (g.K >= 1024) return small ? launch<R, true, 2, 2>(s, batch, g) : launch<R, true, 4, 4>(s, batch, g);
     if (g.M > 64 && !g.herm) return launch<R, false, 8, 4>(s, batch, g);
     return small ? launch<R, false, 2, 2>(s, batch, g) : launch<R, false, 4, 4>(s, batch, g);

@@ -18,6 +18,7 @@ struct GemmArgs {
   cplx<R>* C;
   View vc;  // M x N; vc.conj stores conj(result)
   int herm = 0;  // M == N and the result is Hermitian: only tiles on or below the diagonal are computed
+  int allow_tc = 0;  // complex64 only: route to the tensor-core GEMM when the shape qualifies
 };
 template <typename R>
 cudaError_t gemm(cudaStream_t s, int batch, const GemmArgs<R>& g);

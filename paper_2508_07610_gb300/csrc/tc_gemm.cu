@@ -245,9 +245,7 @@ __global__ void __launch_bounds__(NTH) tc_gemm_kernel(GemmArgs<float> g, int* er
 int* g_err = nullptr;
 }  // namespace
 
-bool tc_gemm_applicable(const GemmArgs<float>& g) {
-  return !g.herm && g.M >= TM && g.N >= 64 && g.K >= TK;
-}
+bool tc_gemm_applicable(const GemmArgs<float>& g) { return !g.herm && g.M >= TM && g.N >= 64 && g.K >= TK; }
 
 cudaError_t tc_gemm(cudaStream_t s, int batch, const GemmArgs<float>& g) {
   if (batch <= 0 || g.M <= 0 || g.N <= 0) return cudaSuccess;

@@ -66,6 +66,7 @@ def lib():
         "mpdo_set_centre": [vp, i32],
         "mpdo_profile": [vp, i32],
         "mpdo_set_neighbour_truncation": [vp, i32],
+        "mpdo_set_tensor_cores": [vp, i32],
         "mpdo_profile_read": [vp, dp, dp, C.POINTER(C.c_longlong)],
     }
     for name, args in sig.items():
@@ -208,6 +209,9 @@ class MPDO:
     def apply_2q_batch(self, q: int, U_dev_ptr: int, ch: ChannelSet, idx_dev_ptr: Optional[int] = None):
         _check(lib().apply_2q_batch(self.h, q, C.c_void_p(U_dev_ptr), ch.h, C.c_void_p(idx_dev_ptr)),
                "apply_2q_batch")
+
+    def set_tensor_cores(self, enable: bool):
+        _check(lib().mpdo_set_tensor_cores(self.h, 1 if enable else 0), "mpdo_set_tensor_cores")
 
     def set_neighbour_truncation(self, enable: bool):
         _check(lib().mpdo_set_neighbour_truncation(self.h, 1 if enable else 0), "mpdo_set_neighbour_truncation")
