@@ -171,7 +171,7 @@ def run_ours(args, torch, rank, world):
     seed = 0x2508076100 + 2 + 1000 * rank
     r = Runner(B, args.prec, sp, seed, depth, torch)
     st = r.st
-    st.set_tensor_cores(not args.no_tc)
+    st.set_tensor_cores(args.tc)
     # ---- reach the steady state: every bond at chi = 64 and every Kraus leg at kappa = 8
     for layer in range(args.saturate):
         r.layer(layer)
@@ -375,7 +375,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp32", "fp64"])
     ap.add_argument("--workload", default="hea", choices=["hea", "qaoa"])
-    ap.add_argument("--no-tc", action="store_true", help="complex64 products on CUDA cores only")
+    ap.add_argument("--tc", action="store_true", help="qualifying complex64 products on the tcgen05 tensor cores")
     ap.add_argument("--instances", type=int, default=4096)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))

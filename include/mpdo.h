@@ -174,7 +174,9 @@ mpdo_status channel_kraus_noalloc(int nq, int count, const double* chi_dev, doub
 /* In the complex64 modes, products with at least 128 rows and 64 columns, an inner dimension of at
  * most 2048 and a non-Hermitian result run on the tensor cores (tcgen05.mma, each FP32 operand split
  * into two TF32 parts, three TF32 products per real product, FP32 accumulation); the others, and
- * every product when this is off, run on the CUDA cores.  On by default; no effect in MPDO_FP64. */
+ * every product when this is off, run on the CUDA cores.  Off by default: the tensor cores' FP32
+ * accumulation leaves about 2e-6 relative error on a 128-long product (the CUDA-core GEMM about 1e-7),
+ * which takes a full-size two-qubit update past 1e-6.  No effect in MPDO_FP64. */
 mpdo_status mpdo_set_tensor_cores(mpdo_t h, int enable);
 
 /* Diagnostic: multiplies random complex64 M x K and K x N matrices with the tensor-core GEMM (tcgen05,

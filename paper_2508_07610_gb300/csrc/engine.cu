@@ -77,7 +77,7 @@ struct EngBase {
   // is not isometric); -1 when every site other than the centre is isometric.
   int dirty = -1;
   bool neighbour_trunc = false;  // let 1q gates on a neighbour of the centre skip the centre move
-  bool tensor_cores = true;      // complex64 products that qualify run on the tcgen05 GEMM
+  bool tensor_cores = false;     // complex64 products that qualify run on the tcgen05 GEMM
   // capture snapshot
   std::vector<int> snap_bond, snap_kraus, snap_slot;
   int snap_centre = 0;
