@@ -175,29 +175,34 @@ def _pair_rdm(sites, q):
 
 
 def per_update_error(st, r, prec):
-    """Accuracy of one full-size update in the benchmark's precision: chain 0's steady state is copied
-    into two one-chain handles, one in the benchmark precision and one in complex128 with FP64
-    eigensolvers; both apply the same noisy CZ on qubits (9, 10), and the largest element difference
-    of the pair's reduced density matrices is returned relative to its trace."""
+    """Accuracy of one full-size update: chain 0's steady state is copied into one-chain handles of
+    each complex64 mode and of complex128 with FP64 eigensolvers; all apply the same noisy CZ on
+    qubits (9, 10), and the largest element difference of the pair's reduced density matrix from the
+    complex128 result is returned relative to its trace.  The complex128 path is run once more on
+    the state rounded to complex64: how far that moves the result is the workload's own sensitivity
+    to a perturbation of the size of complex64 rounding (cuts between nearly equal eigenvalues)."""
     from paper_2508_07610_gb300 import mpdo as G
     from paper_2508_07610_gb300 import workloads as W
 
     sites = st.sites(0)
     q = N_QUBITS // 2 - 1
     rdm = {}
-    for p in (prec, "fp64"):
-        h = G.MPDO(N_QUBITS, CHI, KAPPA, p)
-        for i, a in enumerate(sites):
+    runs = [("fp64", sites), ("fp32", sites), ("mixed", sites),
+            ("fp64_rounded", [a.astype(np.complex64).astype(np.complex128) for a in sites])]
+    for key, ss in runs:
+        h = G.MPDO(N_QUBITS, CHI, KAPPA, key.split("_")[0])
+        for i, a in enumerate(ss):
             h.set_site(i, a)
         # both handles start from the same tensors and gauge; after an odd layer the batched state's
         # centre is at the left end, so declaring it at site 0 is exact
         h.set_centre(0)
         h.apply_2q(q, W.cz(), h.channels(2, [r.chis2[q][0]]))
         h.sync()
-        rdm[p] = _pair_rdm(h.sites(0), q)
+        rdm[key] = _pair_rdm(h.sites(0), q)
         h.free()
     ref = rdm["fp64"]
-    return float(np.max(np.abs(rdm[prec] - ref)) / abs(np.trace(ref)))
+    nrm = abs(np.trace(ref))
+    return {k: float(np.max(np.abs(rdm[k] - ref)) / nrm) for k in ("fp32", "mixed", "fp64_rounded")}
 
 
 def run_ours(args, torch, rank, world):
@@ -353,6 +358,63 @@ def run_qaoa(args, torch, rank, world):
             "n2q_per_pass": run.n_2q()}
 
 
+def run_crosstalk(args, torch, rank, world):
+    """Crosstalk / truncation sweep: one n = 40, depth-20 circuit with simultaneous CZ layers and
+    crosstalk channels on idle neighbouring pairs, run at every (chi, kappa) setting; per setting the
+    2q update rate, the discarded weights, the trace and the purity, compared against the largest
+    setting; and the smallest setting once more in complex128 for the precision comparison."""
+    from paper_2508_07610_gb300 import build as Bld
+    from paper_2508_07610_gb300 import mpdo as G
+    from paper_2508_07610_gb300 import workloads as W
+
+    Bld.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    circ = W.crosstalk_sweep(40, 20, seed=W.MASTER_SEED + 4 + 1000 * rank)
+    n2q = sum(1 for op in circ.ops if op.kind == 2)
+    settings = [tuple(int(v) for v in s.split(",")) for s in args.settings.split(";")]
+
+    def one(chi, kap, prec):
+        st = G.MPDO(circ.n, chi, kap, prec)
+        chans = {}
+        for op in circ.ops:
+            if op.chan not in chans:
+                chans[op.chan] = st.channels(op.kind, [circ.chis[op.chan][1]])
+        st.sync()
+        t0 = time.perf_counter()
+        for op in circ.ops:
+            (st.apply_1q if op.kind == 1 else st.apply_2q)(op.q, op.U, chans[op.chan])
+        st.sync()
+        t = time.perf_counter() - t0
+        t1 = time.perf_counter()
+        pur = float(st.purity()[0])
+        tp = time.perf_counter() - t1
+        bonds, kraus = st.dims()
+        d = st.discarded()[0]
+        row = {"chi": chi, "kappa": kap, "prec": prec, "updates_per_s": n2q / t, "evolve_s": t,
+               "purity": pur, "purity_s": tp, "trace": float(st.trace()[0]), "disc_chi": float(d[0]),
+               "disc_kappa": float(d[1]), "max_bond": max(bonds), "max_kraus": max(kraus),
+               "zz_19_20": float(st.zz(19, 20)[0])}
+        for ch in chans.values():
+            ch.free()
+        st.free()
+        return row
+
+    with ClockSampler(dev.index) as clk:
+        rows = [one(chi, kap, args.prec) for chi, kap in settings]
+    ref = max(rows, key=lambda r: (r["chi"], r["kappa"]))
+    for r in rows:
+        r["purity_minus_largest"] = r["purity"] - ref["purity"]
+        r["zz_minus_largest"] = r["zz_19_20"] - ref["zz_19_20"]
+    small = min(settings)
+    twin = one(small[0], small[1], "fp64") if args.prec != "fp64" else None
+    if twin is not None:
+        base = next(r for r in rows if (r["chi"], r["kappa"]) == small)
+        twin["purity_err_vs_fp64"] = base["purity"] - twin["purity"]
+        twin["disc_err_vs_fp64"] = [base["disc_chi"] - twin["disc_chi"], base["disc_kappa"] - twin["disc_kappa"]]
+    return {"rows": rows, "fp64": twin, "n2q": n2q, "ref": ref, "clocks": clk.summary()}
+
+
 def barrier(torch, world):
     if world > 1:
         torch.distributed.barrier()
@@ -417,7 +479,9 @@ def main():
     ap.add_argument("--cpu-updates", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--prec", default="fp32", choices=["mixed", "fp32", "fp64"])
-    ap.add_argument("--workload", default="hea", choices=["hea", "qaoa"])
+    ap.add_argument("--workload", default="hea", choices=["hea", "qaoa", "crosstalk"])
+    ap.add_argument("--settings", default="32,4;32,8;32,16;64,4;64,8;64,16;128,4;128,8;128,16",
+                    help="crosstalk sweep (chi,kappa) settings")
     ap.add_argument("--tc", action="store_true", help="qualifying complex64 products on the tcgen05 tensor cores")
     ap.add_argument("--instances", type=int, default=4096)
     args = ap.parse_args()
@@ -454,6 +518,21 @@ def main():
     if world > 1:
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         torch.distributed.init_process_group("nccl")
+    if args.workload == "crosstalk":
+        if rank == 0:
+            res = run_crosstalk(args, torch, rank, world)
+            big = res["ref"]
+            line = {"metric": f"2q gate+channel+truncate updates/s, crosstalk sweep n=40 depth 20 at "
+                              f"chi={big['chi']} kappa={big['kappa']}",
+                    "value": big["updates_per_s"], "unit": "updates/s", "n_gpus": 1, "steps": 1, "warmup": 0,
+                    "ms_per_step": 1e3 * big["evolve_s"], "higher_is_better": True, "scaling": "weak",
+                    "vs_baseline": None, "dtype": "c128" if args.prec == "fp64" else "c64", "data": "synthetic",
+                    "config": {"workload": "crosstalk/truncation sweep, n=40, depth 20, one chain per setting",
+                               "n2q": res["n2q"], "precision": args.prec, "settings": res["rows"],
+                               "fp64_twin_of_smallest": res["fp64"]},
+                    "clocks": res["clocks"]}
+            print(json.dumps(line))
+        return
     if args.workload == "qaoa":
         res = run_qaoa(args, torch, rank, world)
         if rank == 0:
@@ -477,19 +556,28 @@ def main():
             torch.distributed.destroy_process_group()
         return
     pk, src = peaks()
-    # dominant kernel class by time
+    # dominant kernel by time: the engine's per-launch CUDA-event record, split by call site
     prof = res["prof"]
-    dom = max(prof, key=lambda k: prof[k][0])
-    ms_d, fl_d, cnt_d = prof[dom]
-    # complex64 arithmetic on CUDA cores: FP32 FMA pipe peak = 152 SMs x 128 lanes x 2 flops x max clock
-    fp32_peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    parts = {k: prof[k] for k in ("gemm_gram", "gemm_theta", "eig_bond", "eig_kraus", "qr", "other")}
+    parts["gemm_rest"] = tuple(prof["gemm"][i] - prof["gemm_gram"][i] - prof["gemm_theta"][i] for i in range(3))
+    parts["eig_rest"] = tuple(prof["eig"][i] - prof["eig_bond"][i] - prof["eig_kraus"][i] for i in range(3))
+    dom = max(parts, key=lambda k: parts[k][0])
+    ms_d, fl_d, cnt_d = parts[dom]
+    # complex64 products and FP32 eigensolvers run on the FP32 FMA pipe: 152 SMs x 128 lanes x 2 flops
+    # x max clock; the FP64 eigensolvers of the mixed mode on the FP64 pipe (nominal 1.25 TFLOP/s)
+    mhz = pk.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+    fp64_eig = args.prec in ("mixed", "fp64") and dom.startswith("eig")
+    peak = 1.25 if (fp64_eig or args.prec == "fp64") else fp32_peak
     achieved = (fl_d / (ms_d / 1e3)) / 1e12 if ms_d > 0 else 0.0
-    roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": None,
-                "peak_source": f"FP32 CUDA-core peak from unit counts x {pk.get('sm_max_mhz', 2070.0):.0f} MHz "
-                               f"({src} peaks file has no FP32 entry)",
+    roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "ms_per_step_in_kernel": ms_d, "launches_per_step": cnt_d,
+                "peak_source": (f"FP32 FMA pipe from unit counts x {mhz:.0f} MHz (the measured-peaks file has "
+                                f"copy bandwidth and bf16 GEMM only)") if peak != 1.25 else
+                               "nominal GB300 FP64 rate (no measured FP64 peak)",
                 "classes": {k: {"ms": v[0], "tflops": (v[1] / (v[0] / 1e3) / 1e12) if v[0] > 0 else None,
-                                "launches": v[2]} for k, v in prof.items()}}
+                                "launches": v[2]} for k, v in parts.items()}}
     cpu = None
     if not args.no_cpu:
         try:
@@ -503,7 +591,8 @@ def main():
     prec_desc = {"mixed": "complex64 contractions, FP64 eigensolvers (MIXED)",
                  "fp32": "complex64 contractions, FP32 eigensolvers", "fp64": "complex128, FP64 eigensolvers"}
     cfg.update({"chains_per_gpu": res["B"], "precision": prec_desc[args.prec],
-                "per_update_rdm_err_vs_fp64": res["upd_err"],
+                "per_update_rdm_err_vs_fp64": res["upd_err"][args.prec] if args.prec != "fp64" else 0.0,
+                "per_update_rdm_err_all_modes": res["upd_err"],
                 "max_abs_zz_err_vs_fp64_after_saturation": res["err"],
                 "note_zz_err": "readouts after many truncating layers of this workload are defined only to "
                                "about 1e-4: its 2q depolarizing channels give 15-fold degenerate Kraus weights, "

@@ -143,11 +143,25 @@ mpdo_status mpdo_set_centre(mpdo_t h, int q);
  * read when each call is made). */
 mpdo_status mpdo_set_neighbour_truncation(mpdo_t h, int enable);
 
-/* Per-launch CUDA-event timing by kernel class (0 GEMM, 1 QR, 2 eigensolver, 3 other), for
- * measurement: enable records an event pair around every launch made outside graph capture;
- * read synchronises and returns, per class, the summed milliseconds, the summed algorithmic
- * flops the engine attributes to those launches (8 real flops per complex multiply-add) and the
- * launch count (arrays of 4), then clears the record. */
+/* Device memory the PURITY readout may hold for its intermediates, in bytes (0, the default: 35% of
+ * the device memory free at its first call).  The purity contraction carries a chi^4 environment
+ * and intermediates of up to 2 kappa chi^5 elements per site; they are processed in chunks of one
+ * environment index sized to this budget, so a smaller budget means more, smaller launches and
+ * the same result.  The buffers are kept until the handle is freed or the budget changes.
+ * MPDO_ENOMEM if not even one chunk fits; MPDO_ESTATE during capture. */
+mpdo_status mpdo_set_purity_memory(mpdo_t h, long long bytes);
+
+/* Per-launch CUDA-event timing by kernel class, for measurement: enable records an event pair
+ * around every launch made outside graph capture; read synchronises and returns, per class, the
+ * summed milliseconds, the summed algorithmic flops the engine attributes to those launches (8 real
+ * flops per complex multiply-add) and the launch count (arrays of MPDO_PROFILE_CLASSES), then clears
+ * the record.  Classes 0-3 partition every launch (GEMM, QR, eigensolver, other); classes 4-7 are
+ * subsets of them, one call site each:
+ *   4  the Kraus-leg Gram G = conj(X) X^T of every kappa truncation (GEMM)
+ *   5  the product X = Y A2 of a two-qubit update, the gate and channel applied to the right site (GEMM)
+ *   6  the bond eigensolver of a two-qubit update (top chi of F')
+ *   7  the Kraus-leg eigensolver of every kappa truncation (top kappa of G) */
+#define MPDO_PROFILE_CLASSES 8
 mpdo_status mpdo_profile(mpdo_t h, int enable);
 mpdo_status mpdo_profile_read(mpdo_t h, double* ms, double* flops, long long* count);
 

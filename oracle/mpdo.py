@@ -154,7 +154,8 @@ class MPDO:
         for i, A in enumerate(self.sites):
             O = ops.get(i)
             B = A if O is None else np.einsum("ab,lbnr->lanr", O, A)
-            E = np.einsum("xy,xpnr,ypns->rs", E, A.conj(), B)
+            X = np.einsum("xy,xpnr->ypnr", E, A.conj(), optimize=True)
+            E = np.einsum("ypnr,ypns->rs", X, B, optimize=True)
         return complex(E[0, 0])
 
     def trace(self) -> float:
@@ -179,7 +180,8 @@ class MPDO:
         """<a| rho |b> for computational basis strings a, b: E'[r,r'] = sum E[l,l'] T[l,a_i,n,r] T*[l',b_i,n,r']."""
         E = np.ones((1, 1), dtype=np.complex128)
         for i, A in enumerate(self.sites):
-            E = np.einsum("xy,xnr,yns->rs", E, A[:, a[i]], A[:, b[i]].conj())
+            X = np.einsum("xy,xnr->ynr", E, A[:, a[i]], optimize=True)
+            E = np.einsum("ynr,yns->rs", X, A[:, b[i]].conj(), optimize=True)
         return complex(E[0, 0])
 
     def ghz_fidelity(self) -> float:
@@ -195,10 +197,11 @@ class MPDO:
         E = np.ones((1, 1, 1, 1), dtype=np.complex128)
         for A in self.sites:
             Ac = A.conj()
-            X = np.einsum("abcd,apnr->bcdpnr", E, A)        # copy 1, ket
-            X = np.einsum("bcdpnr,bqns->cdprqs", X, Ac)     # copy 1, bra (Kraus leg n summed)
-            X = np.einsum("cdprqs,cqmt->dprsmt", X, A)      # copy 2, ket
-            E = np.einsum("dprsmt,dpmu->rstu", X, Ac)       # copy 2, bra (Kraus leg m summed)
+            # one copy at a time (pairwise contractions, each a single BLAS product)
+            X = np.einsum("abcd,apnr->bcdpnr", E, A, optimize=True)        # copy 1, ket
+            X = np.einsum("bcdpnr,bqns->cdprqs", X, Ac, optimize=True)     # copy 1, bra (Kraus leg n summed)
+            X = np.einsum("cdprqs,cqmt->dprsmt", X, A, optimize=True)      # copy 2, ket
+            E = np.einsum("dprsmt,dpmu->rstu", X, Ac, optimize=True)       # copy 2, bra (Kraus leg m summed)
         return E[0, 0, 0, 0].real / self.trace() ** 2
 
     def dense(self) -> np.ndarray:

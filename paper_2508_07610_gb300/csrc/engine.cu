@@ -77,27 +77,31 @@ struct EngBase {
   // is not isometric); -1 when every site other than the centre is isometric.
   int dirty = -1;
   bool neighbour_trunc = false;  // let 1q gates on a neighbour of the centre skip the centre move
+  int64_t purity_limit = 0;      // bytes for the purity chunk buffers, 0 = a share of free memory
   bool tensor_cores = false;     // complex64 products that qualify run on the tcgen05 GEMM
   // capture snapshot
   std::vector<int> snap_bond, snap_kraus, snap_slot;
   int snap_centre = 0;
   // optional per-launch CUDA-event timing by kernel class (not while capturing)
-  enum { P_GEMM = 0, P_QR = 1, P_EIG = 2, P_OTHER = 3, P_N = 4 };
+  enum { P_GEMM = 0, P_QR = 1, P_EIG = 2, P_OTHER = 3, P_GEMM_GRAM = 4, P_GEMM_X = 5, P_EIG_BOND = 6,
+         P_EIG_KRAUS = 7, P_N = 8 };
+  int prof_sub = -1;  // sub-class (one call site) of the next profiled launch, -1 = none
   bool prof_on = false;
   std::vector<cudaEvent_t> ev_pool;
   struct Rec {
-    int cls;
+    int cls, sub;
     int e0, e1;
     double flops;
   };
   std::vector<Rec> recs;
   int ev_next = 0;
-  int cur_cls = -1, cur_e0 = -1;
+  int cur_cls = -1, cur_sub = -1, cur_e0 = -1;
   double cur_flops = 0;
   void prof_start(int cls, double flops) {
     if (!prof_on || capturing) return;
     if (ev_next + 2 > (int)ev_pool.size()) return;
     cur_cls = cls;
+    cur_sub = prof_sub;
     cur_flops = flops;
     cur_e0 = ev_next++;
     cudaEventRecord(ev_pool[cur_e0], stream);
@@ -106,8 +110,20 @@ struct EngBase {
     if (cur_cls < 0) return;
     int e1 = ev_next++;
     cudaEventRecord(ev_pool[e1], stream);
-    recs.push_back({cur_cls, cur_e0, e1, cur_flops});
+    recs.push_back({cur_cls, cur_sub, cur_e0, e1, cur_flops});
     cur_cls = -1;
+  }
+
+  // algorithmic real flops (LAPACK operation counts, complex arithmetic = 4 real per multiply and add):
+  // Householder QR of an m x n matrix with the thin Q formed, p = min(m, n)
+  static double qr_flops(int m, int n) {
+    const double M = m > n ? m : n, P = m < n ? m : n;
+    return 2.0 * 8.0 * (M * P * P - P * P * P / 3.0);
+  }
+  // Hermitian eigenproblem of order n, k vectors: tridiagonalisation + back-transformation
+  static double eig_flops(int n, int k) {
+    const double N = n;
+    return (16.0 / 3.0) * N * N * N + 8.0 * N * N * k;
   }
 
   virtual ~EngBase() {
@@ -162,7 +178,7 @@ struct Eng : EngBase {
   cplx<double>* dDot = nullptr;
   // purity buffers (lazy)
   C *pX = nullptr, *pP = nullptr, *pE = nullptr, *pE2 = nullptr;
-  int64_t pCap = 0, pECap = 0;
+  int64_t pCap = 0, pECap = 0, pLimit = 0;
 
   ~Eng() override {
     void* ptrs[] = {pool, wQR, wQ, wE, wT, wZ, wF, wU, wH, wY, wX, wK, wRt, wF64, wU64, wEval, wScr, dDisc,
@@ -263,7 +279,7 @@ struct Eng : EngBase {
 
   // ---------------------------------------------------------------- kernels wrappers
   mpdo_status gemm_(int M, int N, int K, const C* A, View va, const C* Bm, View vb, C* Cm, View vc, int batch = -1,
-                    int herm = 0) {
+                    int herm = 0, bool accumulate = false) {
     GemmArgs<R> g;
     g.herm = herm;
     g.allow_tc = tensor_cores ? 1 : 0;
@@ -271,7 +287,7 @@ struct Eng : EngBase {
     g.N = N;
     g.K = K;
     g.alpha = mk<R>(1, 0);
-    g.beta = mk<R>(0, 0);
+    g.beta = mk<R>(accumulate ? 1 : 0, 0);
     g.A = A;
     g.va = va;
     g.B = Bm;
@@ -294,6 +310,12 @@ struct Eng : EngBase {
 
   // top-k eigenpairs of the column-major Hermitian matrices in wF (n x n), vectors to wU (col-major n x k)
   mpdo_status eig_(int nmat, int k, int which /*0 chi, 1 kappa, -1 none*/) {
+    prof_sub = which == 0 ? P_EIG_BOND : which == 1 ? P_EIG_KRAUS : -1;
+    mpdo_status st = eig_impl(nmat, k, which);
+    prof_sub = -1;
+    return st;
+  }
+  mpdo_status eig_impl(int nmat, int k, int which) {
     if (std::is_same<R, ER>::value) {
       EigArgs<ER> a;
       a.A = reinterpret_cast<CE*>(wF);
@@ -309,13 +331,18 @@ struct Eng : EngBase {
       a.disc = which >= 0 ? dDisc + which : nullptr;
       a.gap = which >= 0 ? dDisc + 2 : nullptr;
       a.disc_stride = 3;
-      prof_start(P_EIG, 8.0 * (16.0 / 3.0) * nmat * nmat * nmat * B);
+      prof_start(P_EIG, eig_flops(nmat, k) * B);
       CK(heevk<ER>(stream, B, a));
       prof_stop();
       ++launches;
     } else {
       // FP64 eigensolver on complex64 Gram matrices
+      const int sub = prof_sub;
+      prof_sub = -1;
+      prof_start(P_OTHER, 0);
       CK((convert<R, ER>(stream, sF * B, wF, wF64)));
+      prof_stop();
+      prof_sub = sub;
       EigArgs<ER> a;
       a.A = wF64;
       a.astride = sF;
@@ -330,10 +357,14 @@ struct Eng : EngBase {
       a.disc = which >= 0 ? dDisc + which : nullptr;
       a.gap = which >= 0 ? dDisc + 2 : nullptr;
       a.disc_stride = 3;
-      prof_start(P_EIG, 8.0 * (16.0 / 3.0) * nmat * nmat * nmat * B);
+      prof_start(P_EIG, eig_flops(nmat, k) * B);
       CK(heevk<ER>(stream, B, a));
       prof_stop();
+      prof_sub = -1;
+      prof_start(P_OTHER, 0);
       CK((convert<ER, R>(stream, sU * B, wU64, wU)));
+      prof_stop();
+      prof_sub = sub;
       launches += 3;
     }
     return MPDO_OK;
@@ -357,7 +388,7 @@ struct Eng : EngBase {
     a.qstride = sQR;
     a.qout = slot_ptr(sa);
     a.vq = row_major(x, slot_elems);
-    prof_start(P_QR, 8.0 * (4.0 * a.m * a.n * (double)(a.m < a.n ? a.m : a.n)) * B);
+    prof_start(P_QR, qr_flops(a.m, a.n) * B);
     CK(qr<R>(stream, B, a));
     prof_stop();
     ++launches;
@@ -390,7 +421,7 @@ struct Eng : EngBase {
     a.qstride = sQR;
     a.qout = slot_ptr(sa);
     a.vq = v2(slot_elems, 0, 0, 1, 0, 0, L, 1);  // Q^H written as the new x x L site
-    prof_start(P_QR, 8.0 * (4.0 * a.m * a.n * (double)(a.m < a.n ? a.m : a.n)) * B);
+    prof_start(P_QR, qr_flops(a.m, a.n) * B);
     CK(qr<R>(stream, B, a));
     prof_stop();
     ++launches;
@@ -457,8 +488,10 @@ struct Eng : EngBase {
   mpdo_status kappa_truncate_X(int NK, int S, int dr, int kap, int out_slot, const C* Yg = nullptr) {
     const int64_t L = (int64_t)S * dr;
     // G = conj(X) X^T  (NK x NK, column-major, Hermitian: lower triangle computed, upper mirrored)
+    prof_sub = P_GEMM_GRAM;
     mpdo_status st = gemm_(NK, NK, (int)L, wX, v2(sX, 0, 0, L, 0, 0, 1, 1), Yg ? Yg : wX,
                            v2(Yg ? sY : sX, 0, 0, 1, 0, 0, L, 0), wF, col_major(NK, sF), -1, 1);
+    prof_sub = -1;
     if (st) return st;
     prof_start(P_OTHER, 0);
     CK(herm_fill_upper<R>(stream, B, NK, wF, sF));
@@ -584,7 +617,7 @@ struct Eng : EngBase {
     qa.Qw = wQ;
     qa.qstride = sQR;
     qa.qout = nullptr;
-    prof_start(P_QR, 8.0 * (4.0 * qa.m * qa.n * (double)(qa.m < qa.n ? qa.m : qa.n)) * B);
+    prof_start(P_QR, qr_flops(qa.m, qa.n) * B);
     CK(qr<R>(stream, B, qa));
     prof_stop();
     ++launches;
@@ -641,8 +674,10 @@ struct Eng : EngBase {
     // 10. X (Kraus-major [(k, n2)][(b', p2')][r]) = Y . A2
     const int S = 2 * kchi, NK = rk * dn2;
     const int64_t Lx = (int64_t)S * dr;
+    prof_sub = P_GEMM_X;
     st = gemm_(S * rk, K2, C2, wY, row_major(C2, sY), site_ptr(q + 1), row_major(K2, slot_elems), wX,
                v2(sX, rk, dr, (int64_t)dn2 * Lx, dr, Lx, 1));
+    prof_sub = -1;
     if (st) return st;
     // 11-13. Kraus-leg truncation of site q+1
     const int kap = imin(kappa_max, imin((int)Lx, NK));
@@ -829,18 +864,36 @@ struct Eng : EngBase {
   }
 
   // Tr rho^2 by the four-copy transfer (one chain at a time)
+  // Tr rho^2 per chain: a left-to-right sweep of the four-copy environment E[a][b][c][d]
+  // (ket, bra, ket, bra bond indices; D^4 elements) through four GEMMs per site, each about
+  // 2 dn D^5 complex multiply-adds, with permutes between them.  The intermediates are processed in
+  // chunks of the last environment index d (the partial results add up in the final GEMM), so
+  // their size is bounded by a share of the free device memory; the buffers are kept for later calls.
   mpdo_status purity_(std::vector<double>& out) {
     const int64_t X = chi_max, K = kappa_max;
-    const int64_t cap = (2 * K > 4 ? 2 * K : 4) * X * X * X * X;  // largest intermediate, elements
-    if ((double)cap * sizeof(C) > 16e9) return MPDO_ENOMEM;
+    // intermediate elements per unit of d-chunk at the caps
+    auto per_d = [](int64_t D, int64_t dn, int64_t dr) {
+      int64_t u1 = D * D * 2 * dn * dr, u2 = D * 4 * dr * dr, u3 = 2 * dn * dr * dr * dr;
+      int64_t u = u1 > u2 ? u1 : u2;
+      return u > u3 ? u : u3;
+    };
+    const int64_t umax = per_d(X, K, X);
     const int64_t ecap = X * X * X * X;
-    if (pCap < cap) {
+    if (pCap < umax || pLimit != purity_limit) {  // size the chunk buffers (first call or new limit)
+      pLimit = purity_limit;
+      size_t fr = 0, tot = 0;
+      CK(cudaMemGetInfo(&fr, &tot));
       if (pX) cudaFree(pX);
       if (pP) cudaFree(pP);
       pX = pP = nullptr;
-      CK(dmalloc(&pX, cap));
-      CK(dmalloc(&pP, cap));
-      pCap = cap;
+      double budget = 0.35 * (double)fr - 2.0 * (double)ecap * sizeof(C);  // per buffer
+      if (purity_limit > 0) budget = (double)purity_limit / 2.0;
+      int64_t dc = (int64_t)(budget / ((double)umax * sizeof(C)));
+      if (dc < 1) return MPDO_ENOMEM;
+      if (dc > X) dc = X;
+      CK(dmalloc(&pX, dc * umax));
+      CK(dmalloc(&pP, dc * umax));
+      pCap = dc * umax;
     }
     if (pECap < ecap) {
       if (pE) cudaFree(pE);
@@ -857,47 +910,53 @@ struct Eng : EngBase {
       for (int q = 0; q < n; ++q) {
         const int D = bond[q], dn = kraus[q], dr = bond[q + 1];
         const C* A = site_ptr(q) + (int64_t)b * slot_elems;
-        const int64_t D3 = (int64_t)D * D * D;
+        const int64_t D2 = (int64_t)D * D, D3 = D2 * D;
         const int PN = 2 * dn * dr;
-        // X1[(b,c,d)][(p,n,r)] = sum_a E[a][(b,c,d)] A[a][(p,n,r)]
-        mpdo_status st = gemm_((int)D3, PN, D, pE, v2(0, 0, 0, 1, 0, 0, D3), A, row_major(PN, 0), pX, row_major(PN, 0), 1);
-        if (st) return st;
-        // P1[c,d,p,r,b,n] from X1[b,c,d,p,n,r]
-        {
-          int dims[6] = {D, D, D, 2, dn, dr};
-          int perm[6] = {1, 2, 3, 5, 0, 4};
-          CK(permute<R>(stream, 1, 6, dims, perm, pX, 0, pP, 0));
-          ++launches;
+        int64_t Dc = pCap / per_d(D, dn, dr);
+        if (Dc > D) Dc = D;
+        for (int d0 = 0; d0 < D; d0 += (int)Dc) {
+          const int dc = (int)(D - d0 < Dc ? D - d0 : Dc);
+          // X1[(b,c,dd)][(p,n,r)] = sum_a E[a][b][c][d0 + dd] A[a][(p,n,r)]
+          mpdo_status st = gemm_((int)(D2 * dc), PN, D, pE + d0, v2(0, dc, D, 1, 0, 0, D3), A, row_major(PN, 0), pX,
+                                 row_major(PN, 0), 1);
+          if (st) return st;
+          // P1[c,dd,p,r,b,n] from X1[b,c,dd,p,n,r]
+          {
+            int dims[6] = {D, D, dc, 2, dn, dr};
+            int perm[6] = {1, 2, 3, 5, 0, 4};
+            CK(permute<R>(stream, 1, 6, dims, perm, pX, 0, pP, 0));
+            ++launches;
+          }
+          // X2[(c,dd,p,r)][(q,s)] = sum_{(b,n)} P1[(c,dd,p,r)][(b,n)] conj(A[b,q,n,s])
+          const int64_t M2 = (int64_t)D * dc * 2 * dr;
+          st = gemm_((int)M2, 2 * dr, D * dn, pP, row_major((int64_t)D * dn, 0), A,
+                     v2(0, dn, (int64_t)2 * dn * dr, dr, dr, (int64_t)dn * dr, 1, 1), pX, row_major(2 * dr, 0), 1);
+          if (st) return st;
+          // P2[dd,p,r,s,c,q] from X2[c,dd,p,r,q,s]
+          {
+            int dims[6] = {D, dc, 2, dr, 2, dr};
+            int perm[6] = {1, 2, 3, 5, 0, 4};
+            CK(permute<R>(stream, 1, 6, dims, perm, pX, 0, pP, 0));
+            ++launches;
+          }
+          // X3[(dd,p,r,s)][(m,t)] = sum_{(c,q)} P2[(dd,p,r,s)][(c,q)] A[(c,q)][(m,t)]
+          const int64_t M3 = (int64_t)dc * 2 * dr * dr;
+          st = gemm_((int)M3, dn * dr, 2 * D, pP, row_major(2 * D, 0), A, row_major((int64_t)dn * dr, 0), pX,
+                     row_major((int64_t)dn * dr, 0), 1);
+          if (st) return st;
+          // P3[r,s,t,dd,p,m] from X3[dd,p,r,s,m,t]
+          {
+            int dims[6] = {dc, 2, dr, dr, dn, dr};
+            int perm[6] = {2, 3, 5, 0, 1, 4};
+            CK(permute<R>(stream, 1, 6, dims, perm, pX, 0, pP, 0));
+            ++launches;
+          }
+          // E'[(r,s,t)][u] (+)= sum_{(dd,p,m)} P3[(r,s,t)][(dd,p,m)] conj(A[(d0 + dd, p, m)][u])
+          const int64_t M4 = (int64_t)dr * dr * dr;
+          st = gemm_((int)M4, dr, dc * 2 * dn, pP, row_major((int64_t)dc * 2 * dn, 0), A + (int64_t)d0 * 2 * dn * dr,
+                     v2(0, 0, 0, dr, 0, 0, 1, 1), pE2, row_major(dr, 0), 1, 0, d0 > 0);
+          if (st) return st;
         }
-        // X2[(c,d,p,r)][(q,s)] = sum_{(b,n)} P1[(c,d,p,r)][(b,n)] conj(A[b,q,n,s])
-        const int64_t M2 = (int64_t)D * D * 2 * dr;
-        st = gemm_((int)M2, 2 * dr, D * dn, pP, row_major((int64_t)D * dn, 0), A,
-                   v2(0, dn, (int64_t)2 * dn * dr, dr, dr, (int64_t)dn * dr, 1, 1), pX, row_major(2 * dr, 0), 1);
-        if (st) return st;
-        // P2[d,p,r,s,c,q] from X2[c,d,p,r,q,s]
-        {
-          int dims[6] = {D, D, 2, dr, 2, dr};
-          int perm[6] = {1, 2, 3, 5, 0, 4};
-          CK(permute<R>(stream, 1, 6, dims, perm, pX, 0, pP, 0));
-          ++launches;
-        }
-        // X3[(d,p,r,s)][(m,t)] = sum_{(c,q)} P2[(d,p,r,s)][(c,q)] A[(c,q)][(m,t)]
-        const int64_t M3 = (int64_t)D * 2 * dr * dr;
-        st = gemm_((int)M3, dn * dr, 2 * D, pP, row_major(2 * D, 0), A, row_major((int64_t)dn * dr, 0), pX,
-                   row_major((int64_t)dn * dr, 0), 1);
-        if (st) return st;
-        // P3[r,s,t,d,p,m] from X3[d,p,r,s,m,t]
-        {
-          int dims[6] = {D, 2, dr, dr, dn, dr};
-          int perm[6] = {2, 3, 5, 0, 1, 4};
-          CK(permute<R>(stream, 1, 6, dims, perm, pX, 0, pP, 0));
-          ++launches;
-        }
-        // E'[(r,s,t)][u] = sum_{(d,p,m)} P3[(r,s,t)][(d,p,m)] conj(A[(d,p,m)][u])
-        const int64_t M4 = (int64_t)dr * dr * dr;
-        st = gemm_((int)M4, dr, D * 2 * dn, pP, row_major((int64_t)D * 2 * dn, 0), A, v2(0, 0, 0, dr, 0, 0, 1, 1), pE2,
-                   row_major(dr, 0), 1);
-        if (st) return st;
         std::swap(pE, pE2);
       }
       C h;
@@ -1511,6 +1570,13 @@ mpdo_status mpdo_set_neighbour_truncation(mpdo_t h, int enable) {
   return MPDO_OK;
 }
 
+mpdo_status mpdo_set_purity_memory(mpdo_t h, long long bytes) {
+  if (!h || bytes < 0) return MPDO_EINVAL;
+  if (h->e->capturing) return MPDO_ESTATE;
+  h->e->purity_limit = bytes;
+  return MPDO_OK;
+}
+
 mpdo_status mpdo_profile(mpdo_t h, int enable) {
   if (!h) return MPDO_EINVAL;
   EngBase* e = h->e;
@@ -1540,6 +1606,11 @@ mpdo_status mpdo_profile_read(mpdo_t h, double* ms, double* flops, long long* co
     ms[r.cls] += t;
     flops[r.cls] += r.flops;
     count[r.cls] += 1;
+    if (r.sub >= 0) {
+      ms[r.sub] += t;
+      flops[r.sub] += r.flops;
+      count[r.sub] += 1;
+    }
   }
   e->recs.clear();
   e->ev_next = 0;

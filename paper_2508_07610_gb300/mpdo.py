@@ -67,6 +67,7 @@ def lib():
         "mpdo_profile": [vp, i32],
         "mpdo_set_neighbour_truncation": [vp, i32],
         "mpdo_set_tensor_cores": [vp, i32],
+        "mpdo_set_purity_memory": [vp, C.c_longlong],
         "mpdo_profile_read": [vp, dp, dp, C.POINTER(C.c_longlong)],
     }
     for name, args in sig.items():
@@ -181,14 +182,19 @@ class MPDO:
     def profile(self, enable: bool = True):
         _check(lib().mpdo_profile(self.h, 1 if enable else 0), "mpdo_profile")
 
+    PROFILE_CLASSES = ("gemm", "qr", "eig", "other", "gemm_gram", "gemm_theta", "eig_bond", "eig_kraus")
+
     def profile_read(self):
-        """{class: (ms, flops, launches)} for classes gemm, qr, eig, other."""
-        ms, fl = np.zeros(4), np.zeros(4)
-        cnt = np.zeros(4, dtype=np.int64)
+        """{class: (ms, flops, launches)}; gemm, qr, eig and other partition every launch, the last
+        four are single call sites inside them (Kraus-leg Gram, the gate+channel product on the right
+        site, the bond and the Kraus-leg eigensolvers)."""
+        nc = len(self.PROFILE_CLASSES)
+        ms, fl = np.zeros(nc), np.zeros(nc)
+        cnt = np.zeros(nc, dtype=np.int64)
         _check(lib().mpdo_profile_read(self.h, ms.ctypes.data_as(C.POINTER(C.c_double)),
                                        fl.ctypes.data_as(C.POINTER(C.c_double)),
                                        cnt.ctypes.data_as(C.POINTER(C.c_longlong))), "mpdo_profile_read")
-        return {name: (float(ms[i]), float(fl[i]), int(cnt[i])) for i, name in enumerate(("gemm", "qr", "eig", "other"))}
+        return {name: (float(ms[i]), float(fl[i]), int(cnt[i])) for i, name in enumerate(self.PROFILE_CLASSES)}
 
     # -------------------------------------------------------------- channels and gates
     def channels(self, nq: int, chis, tol: float = 1e-12) -> ChannelSet:
@@ -212,6 +218,9 @@ class MPDO:
 
     def set_tensor_cores(self, enable: bool):
         _check(lib().mpdo_set_tensor_cores(self.h, 1 if enable else 0), "mpdo_set_tensor_cores")
+
+    def set_purity_memory(self, nbytes: int):
+        _check(lib().mpdo_set_purity_memory(self.h, C.c_longlong(nbytes)), "mpdo_set_purity_memory")
 
     def set_neighbour_truncation(self, enable: bool):
         _check(lib().mpdo_set_neighbour_truncation(self.h, 1 if enable else 0), "mpdo_set_neighbour_truncation")
