@@ -186,74 +186,77 @@ __global__ void __launch_bounds__(NT) heevk_kernel(EigArgs<R> g) {
   }
   __syncthreads();
 
-  // ---- (3) inverse iteration, one thread per vector t < k
+  // ---- (3) inverse iteration, one thread per vector t < k.  The recurrences carry the running row
+  // (LU) or the running solution entries (substitutions) in registers, so the only memory traffic
+  // inside a recurrence is independent loads of the factors and stores of the results.
   const R pert = eps * fmax(tnorm, R(1e-30));
   for (int t = tid; t < k; t += NT) {
     const R lam = s_w[t];
-    // LU with partial pivoting of T - lam I (diagonals dd, du, du2; multipliers dl; pivots)
-    for (int i = 0; i < n; ++i) {
-      Ldd[(int64_t)i * k + t] = s_d[i] - lam;
-      if (i + 1 < n) {
-        R b = sqrt(s_e2[i]);
-        Ldu[(int64_t)i * k + t] = b;
-        Ldl[(int64_t)i * k + t] = b;
-      }
-      Ldu2[(int64_t)i * k + t] = 0;
-      Lpiv[(int64_t)i * k + t] = 0;
-    }
+    // LU with partial pivoting of T - lam I: factors dd (diagonal of U), du, du2 (its two upper
+    // diagonals), dl (multipliers) and the row interchanges, row by row; (d, u) is the current row
+    R d = s_d[0] - lam;
+    R u = (n > 1) ? sqrt(s_e2[0]) : R(0);
     for (int i = 0; i + 1 < n; ++i) {
-      R di = Ldd[(int64_t)i * k + t], li = Ldl[(int64_t)i * k + t];
-      if (fabs(di) >= fabs(li)) {
-        if (fabs(di) < pert) { di = (di < R(0)) ? -pert : pert; Ldd[(int64_t)i * k + t] = di; }
-        R f = li / di;
-        Ldl[(int64_t)i * k + t] = f;
-        Ldd[(int64_t)(i + 1) * k + t] -= f * Ldu[(int64_t)i * k + t];
+      const R l = sqrt(s_e2[i]);
+      const R dn = s_d[i + 1] - lam;
+      const R un = (i + 2 < n) ? sqrt(s_e2[i + 1]) : R(0);
+      const int64_t o = (int64_t)i * k + t;
+      if (fabs(d) >= fabs(l)) {
+        if (fabs(d) < pert) d = (d < R(0)) ? -pert : pert;
+        const R f = l / d;
+        Ldd[o] = d;
+        Ldu[o] = u;
+        Ldu2[o] = 0;
+        Ldl[o] = f;
+        Lpiv[o] = 0;
+        d = dn - f * u;
+        u = un;
       } else {
-        R f = di / li;
-        Ldd[(int64_t)i * k + t] = li;
-        Ldl[(int64_t)i * k + t] = f;
-        R tmp = Ldu[(int64_t)i * k + t];
-        R dnext = Ldd[(int64_t)(i + 1) * k + t];
-        Ldu[(int64_t)i * k + t] = dnext;
-        Ldd[(int64_t)(i + 1) * k + t] = tmp - f * dnext;
-        if (i + 2 < n) {
-          R unext = Ldu[(int64_t)(i + 1) * k + t];
-          Ldu2[(int64_t)i * k + t] = unext;
-          Ldu[(int64_t)(i + 1) * k + t] = -f * unext;
-        }
-        Lpiv[(int64_t)i * k + t] = 1;
+        const R f = d / l;
+        Ldd[o] = l;
+        Ldu[o] = dn;
+        Ldu2[o] = un;
+        Ldl[o] = f;
+        Lpiv[o] = 1;
+        d = u - f * dn;
+        u = -f * un;
       }
     }
-    {
-      R dl_ = Ldd[(int64_t)(n - 1) * k + t];
-      if (fabs(dl_) < pert) Ldd[(int64_t)(n - 1) * k + t] = (dl_ < R(0)) ? -pert : pert;
-    }
+    if (fabs(d) < pert) d = (d < R(0)) ? -pert : pert;
+    Ldd[(int64_t)(n - 1) * k + t] = d;
     // start vector
     for (int i = 0; i < n; ++i) {
       uint32_t h = hash32((uint32_t)(t * 7919 + 1) * 2654435761u ^ (uint32_t)(i * 40503 + 17));
       Zr[(int64_t)i * k + t] = R((int)(h >> 8) - (1 << 23)) / R(1 << 23);
     }
     for (int it = 0; it < 3; ++it) {
-      // forward: apply L^-1 with the row interchanges
+      // forward: apply L^-1 with the row interchanges; zi is the running entry i
+      R zi = Zr[t];
       for (int i = 0; i + 1 < n; ++i) {
-        R zi = Zr[(int64_t)i * k + t], zn = Zr[(int64_t)(i + 1) * k + t], f = Ldl[(int64_t)i * k + t];
-        if (Lpiv[(int64_t)i * k + t] != R(0)) {
-          Zr[(int64_t)i * k + t] = zn;
-          Zr[(int64_t)(i + 1) * k + t] = zi - f * zn;
+        const int64_t o = (int64_t)i * k + t;
+        const R zn = Zr[o + k], f = Ldl[o];
+        if (Lpiv[o] != R(0)) {
+          Zr[o] = zn;
+          zi = zi - f * zn;
         } else {
-          Zr[(int64_t)(i + 1) * k + t] = zn - f * zi;
+          Zr[o] = zi;
+          zi = zn - f * zi;
         }
       }
-      // backward: U z = y
-      R zmax = 0;
+      Zr[(int64_t)(n - 1) * k + t] = zi;
+      // backward: U z = y; z1, z2 are the solution entries i + 1, i + 2
+      R zmax = 0, z1 = 0, z2 = 0;
       for (int i = n - 1; i >= 0; --i) {
-        R v = Zr[(int64_t)i * k + t];
-        if (i + 1 < n) v -= Ldu[(int64_t)i * k + t] * Zr[(int64_t)(i + 1) * k + t];
-        if (i + 2 < n) v -= Ldu2[(int64_t)i * k + t] * Zr[(int64_t)(i + 2) * k + t];
-        v /= Ldd[(int64_t)i * k + t];
+        const int64_t o = (int64_t)i * k + t;
+        R v = Zr[o];
+        if (i + 1 < n) v -= Ldu[o] * z1;
+        if (i + 2 < n) v -= Ldu2[o] * z2;
+        v /= Ldd[o];
         if (!(fabs(v) < R(1e30))) v = (v > 0) ? R(1e30) : R(-1e30);
-        Zr[(int64_t)i * k + t] = v;
+        Zr[o] = v;
         zmax = fmax(zmax, fabs(v));
+        z2 = z1;
+        z1 = v;
       }
       R sc = (zmax > R(0)) ? R(1) / zmax : R(1);
       R nn = 0;

@@ -3,9 +3,13 @@
 // Every operand is addressed through a View, so site tensors are multiplied in place in whatever
 // index grouping a contraction needs (no permute copies).
 //
-// Tiling: 256 threads per CTA on a 16 x 16 thread grid; each thread owns a TMR x TNC block of
-// contiguous rows and columns of the CTA tile (16 TMR x 16 TNC), operands are staged through shared
-// memory in k-tiles of 16 with the next tile's global loads issued before the current tile is used.
+// Tiling: 256 threads per CTA on a 16 x 16 thread grid.  Thread (ty, tx) owns rows ty*TMR .. +TMR-1
+// and columns tx, tx+16, ..., tx+16(TNC-1) of the CTA tile (16 TMR x 16 TNC), so the B fragment
+// reads of a warp hit consecutive shared-memory words and the C stores of a warp are contiguous.
+// Operands move global -> shared memory with element-wise cp.async (8 or 16 bytes, zero-filled
+// outside the matrix) through a STAGES-deep ring of k-tiles of 16, so loads for later k-tiles are in
+// flight while the current one is multiplied, without staging registers.  The per-row (A) and
+// per-column (B) view offsets of the tile are computed once into shared memory.
 // Long FP32 reductions (K >= 1024, the Gram matrices of the truncations) sum each k-tile into a fresh
 // partial and add it to the running value with Knuth's TwoSum, so their rounding error does not grow
 // with K; the other products accumulate directly.
@@ -15,6 +19,7 @@ namespace mpdo {
 
 namespace {
 constexpr int BK = 16, NT = 256;
+constexpr int PAD = 1;  // one element of padding per k-row: k-fast copies of a warp land in distinct banks
 
 // s + c += x with Knuth's TwoSum: s takes the rounded sum, c collects the exact rounding error
 __device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
@@ -26,12 +31,40 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
 }
 __device__ __forceinline__ void two_sum_acc(double& s, double& c, double x) { s += x; }
 
-template <typename R, bool COMP, int TMR, int TNC>
-__global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs<R> g, int a_m_fast, int b_n_fast) {
-  constexpr int BM = 16 * TMR, BN = 16 * TNC;
-  constexpr int LA = BM * BK / NT, LB = BN * BK / NT;  // elements each thread stages per k-tile
-  __shared__ cplx<R> As[BK][BM];
-  __shared__ cplx<R> Bs[BK][BN];
+// one complex element global -> shared, zero-filled when !valid (src must still be a valid address)
+template <typename R>
+__device__ __forceinline__ void cp_elem(cplx<R>* dst, const cplx<R>* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = valid ? (int)sizeof(cplx<R>) : 0;
+  if constexpr (sizeof(cplx<R>) == 8) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+  }
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <typename R, int TMR, int TNC, int STAGES>
+constexpr size_t smem_bytes() {
+  return sizeof(cplx<R>) * (size_t)STAGES * BK * (16 * TMR + 16 * TNC + 2 * PAD) +
+         sizeof(int64_t) * (16 * TMR + 16 * TNC);
+}
+
+template <typename R, bool COMP, int TMR, int TNC, int STAGES>
+__global__ void __launch_bounds__(NT, 2) gemm_kernel(GemmArgs<R> g, int a_m_fast, int b_n_fast) {
+  constexpr int BM = 16 * TMR, BN = 16 * TNC, SA = BM + PAD, SB = BN + PAD;
+  constexpr int LA = BM * BK / NT, LB = BN * BK / NT;  // elements each thread copies per k-tile
+  static_assert(LA >= 1 && LB >= 1, "tile too small for the thread count");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<R>* As = reinterpret_cast<cplx<R>*>(smem_raw);  // [STAGES][BK][SA]
+  cplx<R>* Bs = As + STAGES * BK * SA;                  // [STAGES][BK][SB]
+  int64_t* rowA = reinterpret_cast<int64_t*>(Bs + STAGES * BK * SB);  // [BM], -1 outside
+  int64_t* colB = rowA + BM;                                          // [BN], -1 outside
+
   const int z = blockIdx.z;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   if (g.herm && n0 > m0 + BM - 1) return;  // tile strictly above the diagonal of a Hermitian result
@@ -40,45 +73,32 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs<R> g, int a_m_fast, i
   cplx<R>* C = g.C + view_batch(g.vc, z);
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
 
-  int64_t aoff[LA];
-  int ai[LA], ak[LA];
-#pragma unroll
-  for (int t = 0; t < LA; ++t) {
-    int e = tid + t * NT;
-    if (a_m_fast) { ai[t] = e % BM; ak[t] = e / BM; } else { ak[t] = e % BK; ai[t] = e / BK; }
-    int i = m0 + ai[t];
-    aoff[t] = (i < g.M) ? view_row(g.va, i) : -1;
-  }
-  int64_t boff[LB];
-  int bj[LB], bk[LB];
-#pragma unroll
-  for (int t = 0; t < LB; ++t) {
-    int e = tid + t * NT;
-    if (b_n_fast) { bj[t] = e % BN; bk[t] = e / BN; } else { bk[t] = e % BK; bj[t] = e / BK; }
-    int j = n0 + bj[t];
-    boff[t] = (j < g.N) ? view_col(g.vb, j) : -1;
-  }
-  cplx<R> ra[LA], rb[LB];
-  auto load_tile = [&](int k0) {
+  for (int i = tid; i < BM; i += NT) rowA[i] = (m0 + i < g.M) ? view_row(g.va, m0 + i) : -1;
+  for (int j = tid; j < BN; j += NT) colB[j] = (n0 + j < g.N) ? view_col(g.vb, n0 + j) : -1;
+  __syncthreads();
+
+  // element e = tid + t * NT of a k-tile is (row, k) = (e % BM, e / BM) when A is row-fast, else
+  // (e / BK, e % BK); likewise for B (tile sizes are powers of two: shifts and masks)
+  auto load_tile = [&](int stage, int k0) {
+    cplx<R>* as = As + stage * BK * SA;
+    cplx<R>* bs = Bs + stage * BK * SB;
 #pragma unroll
     for (int t = 0; t < LA; ++t) {
-      int k = k0 + ak[t];
-      cplx<R> v = mk<R>(0, 0);
-      if (aoff[t] >= 0 && k < g.K) {
-        v = A[aoff[t] + view_col(g.va, k)];
-        if (g.va.conj) v.y = -v.y;
-      }
-      ra[t] = v;
+      const int e = tid + t * NT;
+      const int ai = a_m_fast ? e % BM : e / BK, ak = a_m_fast ? e / BM : e % BK;
+      const int k = k0 + ak;
+      const int64_t ro = rowA[ai];
+      const bool ok = ro >= 0 && k < g.K;
+      cp_elem(as + ak * SA + ai, ok ? A + ro + view_col(g.va, k) : A, ok);
     }
 #pragma unroll
     for (int t = 0; t < LB; ++t) {
-      int k = k0 + bk[t];
-      cplx<R> v = mk<R>(0, 0);
-      if (boff[t] >= 0 && k < g.K) {
-        v = B[boff[t] + view_row(g.vb, k)];
-        if (g.vb.conj) v.y = -v.y;
-      }
-      rb[t] = v;
+      const int e = tid + t * NT;
+      const int bj = b_n_fast ? e % BN : e / BK, bk = b_n_fast ? e / BN : e % BK;
+      const int k = k0 + bk;
+      const int64_t co = colB[bj];
+      const bool ok = co >= 0 && k < g.K;
+      cp_elem(bs + bk * SB + bj, ok ? B + co + view_row(g.vb, k) : B, ok);
     }
   };
 
@@ -93,33 +113,53 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs<R> g, int a_m_fast, i
 #pragma unroll
       for (int c = 0; c < TNC; ++c) comp[r][c] = mk<R>(0, 0);
   }
+  const bool conjA = g.va.conj != 0, conjB = g.vb.conj != 0;
 
-  load_tile(0);
-  for (int k0 = 0; k0 < g.K; k0 += BK) {
+  const int nk = (g.K + BK - 1) / BK;
 #pragma unroll
-    for (int t = 0; t < LA; ++t) As[ak[t]][ai[t]] = ra[t];
-#pragma unroll
-    for (int t = 0; t < LB; ++t) Bs[bk[t]][bj[t]] = rb[t];
-    __syncthreads();
-    if (k0 + BK < g.K) load_tile(k0 + BK);  // next tile's loads in flight during the products
+  for (int s = 0; s < STAGES - 1; ++s) {
+    if (s < nk) load_tile(s, s * BK);
+    cp_commit();
+  }
+  for (int kt = 0; kt < nk; ++kt) {
+    cp_wait<STAGES - 2>();
+    __syncthreads();  // tile kt is in shared memory for every thread; stage (kt - 1) is free
+    {
+      const int pf = kt + STAGES - 1;
+      if (pf < nk) load_tile(pf % STAGES, pf * BK);
+      cp_commit();
+    }
+    const cplx<R>* as = As + (kt % STAGES) * BK * SA;
+    const cplx<R>* bs = Bs + (kt % STAGES) * BK * SB;
+    cplx<R> part[COMP ? TMR : 1][COMP ? TNC : 1];
     if constexpr (COMP) {
-      cplx<R> part[TMR][TNC];
 #pragma unroll
       for (int r = 0; r < TMR; ++r)
 #pragma unroll
         for (int c = 0; c < TNC; ++c) part[r][c] = mk<R>(0, 0);
+    }
 #pragma unroll 4
-      for (int kk = 0; kk < BK; ++kk) {
-        cplx<R> a[TMR], b[TNC];
+    for (int kk = 0; kk < BK; ++kk) {
+      cplx<R> a[TMR], b[TNC];
 #pragma unroll
-        for (int r = 0; r < TMR; ++r) a[r] = As[kk][ty * TMR + r];
-#pragma unroll
-        for (int c = 0; c < TNC; ++c) b[c] = Bs[kk][tx * TNC + c];
-#pragma unroll
-        for (int r = 0; r < TMR; ++r)
-#pragma unroll
-          for (int c = 0; c < TNC; ++c) cfma(part[r][c], a[r], b[c]);
+      for (int r = 0; r < TMR; ++r) {
+        a[r] = as[kk * SA + ty * TMR + r];
+        if (conjA) a[r].y = -a[r].y;
       }
+#pragma unroll
+      for (int c = 0; c < TNC; ++c) {
+        b[c] = bs[kk * SB + tx + 16 * c];
+        if (conjB) b[c].y = -b[c].y;
+      }
+#pragma unroll
+      for (int r = 0; r < TMR; ++r)
+#pragma unroll
+        for (int c = 0; c < TNC; ++c) {
+          if constexpr (COMP) cfma(part[r][c], a[r], b[c]);
+          else cfma(acc[r][c], a[r], b[c]);
+        }
+    }
+    if constexpr (COMP) {
 #pragma unroll
       for (int r = 0; r < TMR; ++r)
 #pragma unroll
@@ -127,34 +167,21 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs<R> g, int a_m_fast, i
           two_sum_acc(acc[r][c].x, comp[r][c].x, part[r][c].x);
           two_sum_acc(acc[r][c].y, comp[r][c].y, part[r][c].y);
         }
-    } else {
-#pragma unroll 4
-      for (int kk = 0; kk < BK; ++kk) {
-        cplx<R> a[TMR], b[TNC];
-#pragma unroll
-        for (int r = 0; r < TMR; ++r) a[r] = As[kk][ty * TMR + r];
-#pragma unroll
-        for (int c = 0; c < TNC; ++c) b[c] = Bs[kk][tx * TNC + c];
-#pragma unroll
-        for (int r = 0; r < TMR; ++r)
-#pragma unroll
-          for (int c = 0; c < TNC; ++c) cfma(acc[r][c], a[r], b[c]);
-      }
     }
-    __syncthreads();
   }
+  cp_wait<0>();
 
   const bool use_beta = (g.beta.x != R(0) || g.beta.y != R(0));
 #pragma unroll
   for (int r = 0; r < TMR; ++r) {
-    int i = m0 + ty * TMR + r;
+    const int i = m0 + ty * TMR + r;
     if (i >= g.M) continue;
-    int64_t ro = view_row(g.vc, i);
+    const int64_t ro = view_row(g.vc, i);
 #pragma unroll
     for (int c = 0; c < TNC; ++c) {
-      int j = n0 + tx * TNC + c;
+      const int j = n0 + tx + 16 * c;
       if (j >= g.N) continue;
-      int64_t o = ro + view_col(g.vc, j);
+      const int64_t o = ro + view_col(g.vc, j);
       cplx<R> sum = acc[r][c];
       if constexpr (COMP) sum = sum + comp[r][c];
       cplx<R> v = g.alpha * sum;
@@ -172,10 +199,20 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs<R> g, int a_m_fast, i
 template <typename R, bool COMP, int TMR, int TNC>
 cudaError_t launch(cudaStream_t s, int batch, const GemmArgs<R>& g) {
   constexpr int BM = 16 * TMR, BN = 16 * TNC;
-  int a_m_fast = (g.va.rdiv == 0 && g.va.rlo == 1) ? 1 : 0;
-  int b_n_fast = (g.vb.cdiv == 0 && g.vb.clo == 1) ? 1 : 0;
+  // three stages for complex64, two for complex128 (twice the bytes per element)
+  constexpr int STAGES = sizeof(R) == 4 ? 3 : 2;
+  constexpr size_t bytes = smem_bytes<R, TMR, TNC, STAGES>();
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(gemm_kernel<R, COMP, TMR, TNC, STAGES>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int a_m_fast = (g.va.rdiv == 0 && g.va.rlo == 1) ? 1 : 0;
+  const int b_n_fast = (g.vb.cdiv == 0 && g.vb.clo == 1) ? 1 : 0;
   dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, batch);
-  gemm_kernel<R, COMP, TMR, TNC><<<grid, NT, 0, s>>>(g, a_m_fast, b_n_fast);
+  gemm_kernel<R, COMP, TMR, TNC, STAGES><<<grid, NT, bytes, s>>>(g, a_m_fast, b_n_fast);
   return cudaGetLastError();
 }
 }  // namespace

@@ -318,6 +318,287 @@ __global__ void __launch_bounds__(NT) qr_cluster_kernel(QrArgs<R> g, int C, int 
   cluster.sync();  // no CTA leaves while a peer may still read its shared memory
 }
 
+// ---------------------------------------------------------------------------------------------
+// Blocked variant (throughput path for many matrices): reflectors are generated NB columns at a
+// time on a panel held in shared memory and applied to the rest of the matrix as one block reflector
+// I - V T V^H (compact WY form: T upper triangular with T_jj = beta_j and
+// T[0:j, j] = -beta_j T[0:j, 0:j] V[:, 0:j]^H v_j), so every pass over the trailing columns serves NB
+// reflectors instead of one and runs as two small matrix products with V in shared memory.  Q is
+// accumulated the same way, panels last to first.
+//
+// Ws[i * ldw + c] = (V^H A)[i][c] over a block of columns, A column-major (ld lda, rows 0..M-1 of
+// the block), V = the panel's pb reflectors in shared memory (column i at Vs + i * ldv).
+template <typename R, int NB>
+__device__ void panel_vh_times(const cplx<R>* A, int64_t lda, int M, int nc, const cplx<R>* Vs, int ldv, int pb,
+                               cplx<R>* Ws, int ldw) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int c0 = 2 * wid; c0 < nc; c0 += 2 * (NT / 32)) {
+    const bool two = c0 + 1 < nc;
+    cplx<R> acc0[NB], acc1[NB];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) acc0[i] = acc1[i] = mk<R>(0, 0);
+    const cplx<R>* a0p = A + (int64_t)c0 * lda;
+    const cplx<R>* a1p = a0p + lda;
+    for (int r = lane; r < M; r += 32) {
+      const cplx<R> a0 = a0p[r];
+      const cplx<R> a1 = two ? a1p[r] : mk<R>(0, 0);
+#pragma unroll
+      for (int i = 0; i < NB; ++i) {
+        if (i < pb) {
+          const cplx<R> v = Vs[i * ldv + r];
+          cfma_cj(acc0[i], v, a0);
+          cfma_cj(acc1[i], v, a1);
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      if (i < pb) {
+        const cplx<R> s0 = warp_csum(acc0[i]);
+        const cplx<R> s1 = warp_csum(acc1[i]);
+        if (lane == 0) {
+          Ws[i * ldw + c0] = s0;
+          if (two) Ws[i * ldw + c0 + 1] = s1;
+        }
+      }
+    }
+  }
+}
+
+// A -= V Y over a block of columns, Y[i][c] = Ws[i * ldw + c].
+template <typename R, int NB>
+__device__ void panel_minus_v_times(cplx<R>* A, int64_t lda, int M, int nc, const cplx<R>* Vs, int ldv, int pb,
+                                    const cplx<R>* Ws, int ldw) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int c0 = 2 * wid; c0 < nc; c0 += 2 * (NT / 32)) {
+    const bool two = c0 + 1 < nc;
+    cplx<R> y0[NB], y1[NB];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      y0[i] = (i < pb) ? Ws[i * ldw + c0] : mk<R>(0, 0);
+      y1[i] = (i < pb && two) ? Ws[i * ldw + c0 + 1] : mk<R>(0, 0);
+    }
+    cplx<R>* a0p = A + (int64_t)c0 * lda;
+    cplx<R>* a1p = a0p + lda;
+    for (int r = lane; r < M; r += 32) {
+      cplx<R> s0 = mk<R>(0, 0), s1 = mk<R>(0, 0);
+#pragma unroll
+      for (int i = 0; i < NB; ++i) {
+        if (i < pb) {
+          const cplx<R> v = Vs[i * ldv + r];
+          cfma(s0, v, y0[i]);
+          cfma(s1, v, y1[i]);
+        }
+      }
+      a0p[r] = a0p[r] - s0;
+      if (two) a1p[r] = a1p[r] - s1;
+    }
+  }
+}
+
+// Ws[., c] <- T^H Ws[., c] (herm) or T Ws[., c]; T upper triangular pb x pb, column-major, ld NB
+template <typename R, int NB>
+__device__ void panel_apply_t(const cplx<R>* T, int pb, bool herm, cplx<R>* Ws, int ldw, int nc) {
+  for (int c = threadIdx.x; c < nc; c += NT) {
+    cplx<R> w[NB], y[NB];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) w[i] = (i < pb) ? Ws[i * ldw + c] : mk<R>(0, 0);
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      cplx<R> acc = mk<R>(0, 0);
+      if (herm) {
+#pragma unroll
+        for (int k = 0; k <= i; ++k) cfma_cj(acc, T[k + i * NB], w[k]);  // (T^H)[i][k] = conj(T[k][i])
+      } else {
+#pragma unroll
+        for (int k = i; k < NB; ++k) cfma(acc, T[i + k * NB], w[k]);
+      }
+      y[i] = acc;
+    }
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+      if (i < pb) Ws[i * ldw + c] = y[i];
+  }
+}
+
+template <typename R, int NB>
+size_t blocked_smem_bytes(int m, int n) {
+  const int x = m < n ? m : n;
+  const int npan = (x + NB - 1) / NB;
+  return sizeof(cplx<R>) * ((size_t)NB * m + (size_t)npan * NB * NB + (size_t)NB * n + x) +
+         sizeof(R) * ((size_t)x + NT / 32);
+}
+
+template <typename R, int NB>
+__global__ void __launch_bounds__(NT) qr_blocked_kernel(QrArgs<R> g) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int z = blockIdx.x;
+  const int m = g.m, n = g.n, x = (m < n) ? m : n;
+  const int npan = (x + NB - 1) / NB;
+  cplx<R>* Vs = reinterpret_cast<cplx<R>*>(smem_raw);  // NB panel columns, ld m (rows relative to p0)
+  cplx<R>* Ts = Vs + (size_t)NB * m;                    // T of every panel, NB x NB column-major
+  cplx<R>* Ws = Ts + (size_t)npan * NB * NB;            // NB x n products (row i at Ws + i * n)
+  cplx<R>* s_v0 = Ws + (size_t)NB * n;                  // x reflector heads
+  R* s_beta = reinterpret_cast<R*>(s_v0 + x);           // x
+  R* red = s_beta + x;                                  // NT / 32
+  cplx<R>* W = g.W + (int64_t)z * g.wstride;
+  cplx<R>* Q = g.Qw + (int64_t)z * g.qstride;
+  const cplx<R>* in = g.in + view_batch(g.vin, z);
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+
+  for (int64_t e = tid; e < (int64_t)m * n; e += NT) {
+    int i = (int)(e % m), j = (int)(e / m);
+    cplx<R> v = in[view_row(g.vin, i) + view_col(g.vin, j)];
+    if (g.vin.conj) v.y = -v.y;
+    W[e] = v;
+  }
+  __syncthreads();
+
+  for (int P = 0; P < npan; ++P) {
+    const int p0 = P * NB, pb = (x - p0 < NB) ? x - p0 : NB, M = m - p0;
+    for (int e = tid; e < pb * M; e += NT) {
+      int i = e / M, r = e % M;
+      Vs[i * m + r] = W[(int64_t)(p0 + i) * m + p0 + r];
+    }
+    __syncthreads();
+    // factor the panel in shared memory
+    for (int jj = 0; jj < pb; ++jj) {
+      cplx<R>* col = Vs + jj * m;
+      R s = 0;
+      for (int r = jj + 1 + tid; r < M; r += NT) s += norm2(col[r]);
+      s = block_sum(s, red);
+      const cplx<R> a = col[jj];
+      const R aa = sqrt(norm2(a));
+      const R nrm = sqrt(aa * aa + s);
+      const cplx<R> ph = (aa > R(0)) ? mk<R>(a.x / aa, a.y / aa) : mk<R>(1, 0);
+      const R beta = (nrm > tiny_norm<R>()) ? R(1) / (nrm * (nrm + aa)) : R(0);
+      const cplx<R> v0 = a + nrm * ph;
+      if (beta != R(0)) {
+        for (int c = jj + 1 + wid; c < pb; c += NT / 32) {
+          cplx<R>* y = Vs + c * m;
+          cplx<R> acc = mk<R>(0, 0);
+          if (lane == 0) cfma_cj(acc, v0, y[jj]);
+          for (int r = jj + 1 + lane; r < M; r += 32) cfma_cj(acc, col[r], y[r]);
+          acc = warp_csum(acc);
+          acc = beta * acc;
+          if (lane == 0) y[jj] = y[jj] - v0 * acc;
+          for (int r = jj + 1 + lane; r < M; r += 32) y[r] = y[r] - col[r] * acc;
+        }
+      }
+      __syncthreads();
+      // column p0 + jj: R entries (rows p0 .. p0 + jj) and the reflector below go back to W; the
+      // shared copy becomes the full reflector (zeros above, v0 on the diagonal)
+      cplx<R>* wc = W + (int64_t)(p0 + jj) * m + p0;
+      for (int r = tid; r < M; r += NT) {
+        if (r < jj) {
+          wc[r] = col[r];
+          col[r] = mk<R>(0, 0);
+        } else if (r > jj) {
+          wc[r] = col[r];
+        }
+      }
+      if (tid == 0) {
+        wc[jj] = (beta != R(0)) ? mk<R>(-nrm * ph.x, -nrm * ph.y) : a;
+        col[jj] = v0;
+        s_beta[p0 + jj] = beta;
+        s_v0[p0 + jj] = v0;
+      }
+      __syncthreads();
+    }
+    // T of the panel: S[i][k] = v_i^H v_k (i < k; v_k vanishes above row k), then the recurrence
+    cplx<R>* T = Ts + (size_t)P * NB * NB;
+    cplx<R>* S = Ws;  // NB x NB scratch, S[i * NB + k]
+    for (int pr = wid; pr < pb * pb; pr += NT / 32) {
+      const int i = pr / pb, k = pr % pb;
+      if (i >= k) continue;
+      cplx<R> acc = mk<R>(0, 0);
+      for (int r = k + lane; r < M; r += 32) cfma_cj(acc, Vs[i * m + r], Vs[k * m + r]);
+      acc = warp_csum(acc);
+      if (lane == 0) S[i * NB + k] = acc;
+    }
+    __syncthreads();
+    for (int k = 0; k < NB; ++k) {
+      if (tid < NB) {
+        const int i = tid;
+        cplx<R> t = mk<R>(0, 0);
+        if (k < pb && i < k) {
+          cplx<R> acc = mk<R>(0, 0);
+          for (int l = i; l < k; ++l) cfma(acc, T[i + l * NB], S[l * NB + k]);
+          t = -s_beta[p0 + k] * acc;
+        } else if (k < pb && i == k) {
+          t = mk<R>(s_beta[p0 + k], 0);
+        }
+        T[i + k * NB] = t;
+      }
+      __syncthreads();
+    }
+    // trailing columns: A <- (I - V T^H V^H) A on rows p0.., columns p0 + pb ..
+    const int nc = n - p0 - pb;
+    if (nc > 0) {
+      cplx<R>* A = W + (int64_t)(p0 + pb) * m + p0;
+      panel_vh_times<R, NB>(A, m, M, nc, Vs, m, pb, Ws, n);
+      __syncthreads();
+      panel_apply_t<R, NB>(T, pb, true, Ws, n, nc);
+      __syncthreads();
+      panel_minus_v_times<R, NB>(A, m, M, nc, Vs, m, pb, Ws, n);
+      __syncthreads();
+    }
+  }
+
+  // Q = H_0 H_1 ... H_{x-1} [I; 0], one block reflector I - V T V^H per panel, last panel first
+  for (int64_t e = tid; e < (int64_t)m * x; e += NT) {
+    int i = (int)(e % m), c = (int)(e / m);
+    Q[e] = mk<R>(i == c ? R(1) : R(0), R(0));
+  }
+  __syncthreads();
+  for (int P = npan - 1; P >= 0; --P) {
+    const int p0 = P * NB, pb = (x - p0 < NB) ? x - p0 : NB, M = m - p0;
+    for (int e = tid; e < pb * M; e += NT) {
+      int i = e / M, r = e % M;
+      cplx<R> v = mk<R>(0, 0);
+      if (r == i) v = s_v0[p0 + i];
+      else if (r > i) v = W[(int64_t)(p0 + i) * m + p0 + r];
+      Vs[i * m + r] = v;
+    }
+    __syncthreads();
+    const int nc = x - p0;
+    cplx<R>* A = Q + (int64_t)p0 * m + p0;
+    panel_vh_times<R, NB>(A, m, M, nc, Vs, m, pb, Ws, n);
+    __syncthreads();
+    panel_apply_t<R, NB>(Ts + (size_t)P * NB * NB, pb, false, Ws, n, nc);
+    __syncthreads();
+    panel_minus_v_times<R, NB>(A, m, M, nc, Vs, m, pb, Ws, n);
+    __syncthreads();
+  }
+  // R: clear the reflectors below the diagonal of the leading x rows.
+  for (int64_t e = tid; e < (int64_t)x * x; e += NT) {
+    int i = (int)(e % x), j = (int)(e / x);
+    if (i > j) W[(int64_t)j * m + i] = mk<R>(0, 0);
+  }
+  if (g.qout) {
+    cplx<R>* out = g.qout + view_batch(g.vq, z);
+    for (int64_t e = tid; e < (int64_t)m * x; e += NT) {
+      int i = (int)(e % m), c = (int)(e / m);
+      cplx<R> v = Q[e];
+      if (g.vq.conj) v.y = -v.y;
+      out[view_row(g.vq, i) + view_col(g.vq, c)] = v;
+    }
+  }
+}
+
+template <typename R, int NB>
+cudaError_t launch_blocked(cudaStream_t s, int batch, const QrArgs<R>& g, size_t bytes) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e =
+        cudaFuncSetAttribute(qr_blocked_kernel<R, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  qr_blocked_kernel<R, NB><<<batch, NT, bytes, s>>>(g);
+  return cudaGetLastError();
+}
+
 template <typename R>
 size_t cluster_smem_bytes(int mloc, int n) {
   return sizeof(cplx<R>) * ((size_t)mloc * n + 2 * (n + 2) + 2 * (size_t)n) + sizeof(R) * ((size_t)n + NT / 32) + 64;
@@ -367,6 +648,12 @@ cudaError_t qr(cudaStream_t s, int batch, const QrArgs<R>& g) {
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
   }
+  // many matrices: the blocked kernel with the widest panel whose shared memory fits
+  constexpr size_t kBlockedBudget = 200 * 1024;
+  constexpr int NB1 = sizeof(R) == 4 ? 16 : 8, NB2 = NB1 / 2;
+  const size_t b1 = blocked_smem_bytes<R, NB1>(g.m, g.n), b2 = blocked_smem_bytes<R, NB2>(g.m, g.n);
+  if (b1 <= kBlockedBudget) return launch_blocked<R, NB1>(s, batch, g, b1);
+  if (b2 <= kBlockedBudget) return launch_blocked<R, NB2>(s, batch, g, b2);
   qr_kernel<R><<<batch, NT, 0, s>>>(g);
   return cudaGetLastError();
 }

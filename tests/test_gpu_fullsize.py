@@ -34,8 +34,8 @@ def _state(seed):
     return W.random_right_canonical_sites(N, CHI, KAP, rng)
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-6), ("fp32", 1e-6)])
-def test_single_update_full_size(prec, tol):
+@pytest.fixture(scope="module")
+def one_update():
     sites = _state(2026)
     chi2 = W.kraus_to_chi(W.compose(W.depolarizing_2q(1e-2), W.unitary_channel(W.zz_phase(0.013))))
     q = 9
@@ -43,8 +43,16 @@ def test_single_update_full_size(prec, tol):
     orc.sites = [s.copy() for s in sites]
     orc.centre = 0
     orc.apply_2q(q, W.cz(), OC.chi_to_kraus(chi2, 2))
+    return sites, chi2, q, orc
 
-    st = G.MPDO(N, CHI, KAP, prec)
+
+@pytest.mark.parametrize("batch", [1, 160])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-6), ("fp32", 1e-6)])
+def test_single_update_full_size(prec, tol, batch, one_update):
+    """batch = 160 runs the same update on 160 identical chains: more matrices than the GPU has SMs
+    for the cluster QR, so the centre moves and the reduction take the blocked one-CTA-per-matrix QR."""
+    sites, chi2, q, orc = one_update
+    st = G.MPDO(N, CHI, KAP, prec, batch=batch)
     for i, s in enumerate(sites):
         st.set_site(i, s)
     st.set_centre(0)
@@ -52,19 +60,28 @@ def test_single_update_full_size(prec, tol):
     st.apply_2q(q, W.cz(), ch)
     st.sync()
 
-    d = st.discarded()[0]
-    assert abs(d[0] - orc.discarded_chi) < tol, (d[0], orc.discarded_chi)
-    assert abs(d[1] - orc.discarded_kappa) < tol, (d[1], orc.discarded_kappa)
     bg, kg = st.dims()
     assert bg == orc.bond_dims() and kg == orc.kraus_dims()
-    r_g = _pair_rdm(st.get_site(q), st.get_site(q + 1))
     r_o = _pair_rdm(orc.sites[q], orc.sites[q + 1])
     scale = np.trace(r_o).real
-    err = np.max(np.abs(r_g - r_o)) / scale
-    print(f"full-size single update {prec}: rdm err {err:.2e}, discarded {d[0]:.3e} / {d[1]:.3e}")
-    assert err < tol
-    zz = st.zz(q, q + 1)[0]
-    assert abs(zz - orc.expect_zz(q, q + 1)) < tol
+    disc = st.discarded()
+    zz = st.zz(q, q + 1)
+    first = None
+    for b in sorted({0, batch // 2, batch - 1}):
+        d = disc[b]
+        assert abs(d[0] - orc.discarded_chi) < tol, (b, d[0], orc.discarded_chi)
+        assert abs(d[1] - orc.discarded_kappa) < tol, (b, d[1], orc.discarded_kappa)
+        r_g = _pair_rdm(st.get_site(q, b), st.get_site(q + 1, b))
+        err = np.max(np.abs(r_g - r_o)) / scale
+        print(f"full-size single update {prec} batch {batch} chain {b}: rdm err {err:.2e}, "
+              f"discarded {d[0]:.3e} / {d[1]:.3e}")
+        assert err < tol
+        assert abs(zz[b] - orc.expect_zz(q, q + 1)) < tol
+        # identical chains give identical results
+        if first is None:
+            first = r_g
+        else:
+            assert np.array_equal(r_g, first)
 
 
 def _perturbed(circ, rel, seed):
