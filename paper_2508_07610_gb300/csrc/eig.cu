@@ -72,7 +72,7 @@ __device__ int sturm_count(const R* d, const R* e2, int n, R sigma, R pivmin) {
   return cnt;
 }
 
-template <typename R>
+template <typename R, int NB>
 __global__ void __launch_bounds__(NT) heevk_kernel(EigArgs<R> g) {
   __shared__ R red[NT / 32];
   __shared__ R s_d[MAXN], s_e2[MAXN], s_beta[MAXN];
@@ -95,48 +95,102 @@ __global__ void __launch_bounds__(NT) heevk_kernel(EigArgs<R> g) {
   cplx<R>* U = reinterpret_cast<cplx<R>*>(Zr + (int64_t)n * k);   // complex, vector t column at [t * n]
   cplx<R>* PH = U + (int64_t)n * k;                                  // phases, n
 
-  // ---- (1) tridiagonalisation: A <- H A H on the trailing block, H = I - beta v v^H
-  for (int j = 0; j + 2 < n; ++j) {
-    cplx<R>* col = A + (int64_t)j * n;
-    R s = 0;
-    for (int i = j + 2 + tid; i < n; i += NT) s += norm2(col[i]);
-    s = block_sum(s, red);
-    const cplx<R> a = col[j + 1];
-    const R aa = sqrt(norm2(a));
-    const R nrm = sqrt(aa * aa + s);
-    const cplx<R> ph = (aa > R(0)) ? mk<R>(a.x / aa, a.y / aa) : mk<R>(1, 0);
-    const R beta = (nrm > tiny_norm<R>()) ? R(1) / (nrm * (nrm + aa)) : R(0);
-    const cplx<R> v0 = a + nrm * ph;
-    for (int i = j + 1 + tid; i < n; i += NT) s_v[i] = (i == j + 1) ? v0 : col[i];
-    if (tid == 0) s_beta[j] = beta;
-    __syncthreads();
-    if (beta != R(0)) {
-      // p = beta * A_sub v
-      for (int i = j + 1 + tid; i < n; i += NT) {
-        cplx<R> acc = mk<R>(0, 0);
-        for (int c = j + 1; c < n; ++c) cfma(acc, A[(int64_t)c * n + i], s_v[c]);
-        s_p[i] = beta * acc;
+  // ---- (1) tridiagonalisation: A <- H A H on the trailing block, H = I - beta v v^H, in panels of
+  // NB reflectors.  Inside a panel the trailing block is not updated: column j is brought up to date
+  // from the panel's earlier pairs (v_l, w_l) when it is reached, and the product with the block uses
+  // A v - V (W^H v) - W (V^H v).  At the end of the panel the whole rank-2 NB update is applied in one
+  // pass (the blocked reduction of LAPACK's Hermitian tridiagonalisation).
+  extern __shared__ __align__(16) unsigned char eig_dyn[];
+  cplx<R>* Vb = reinterpret_cast<cplx<R>*>(eig_dyn);  // NB x n, reflector l at Vb + l * n
+  cplx<R>* Wb = Vb + (size_t)NB * n;                  // NB x n
+  __shared__ cplx<R> s_x[2 * NB];
+  for (int j0 = 0; j0 + 2 < n; j0 += NB) {
+    const int pb = (n - 2 - j0 < NB) ? n - 2 - j0 : NB;
+    for (int jj = 0; jj < pb; ++jj) {
+      const int j = j0 + jj;
+      cplx<R>* col = A + (int64_t)j * n;
+      // column j (rows j..n-1) brought up to date and written back
+      for (int i = j + tid; i < n; i += NT) {
+        cplx<R> c = col[i];
+        for (int l = 0; l < jj; ++l) {
+          c = c - Vb[l * n + i] * conjg(Wb[l * n + j]);
+          c = c - Wb[l * n + i] * conjg(Vb[l * n + j]);
+        }
+        col[i] = c;
       }
       __syncthreads();
-      // K = (beta / 2) v^H p ; w = p - K v
-      cplx<R> part = mk<R>(0, 0);
-      for (int i = j + 1 + tid; i < n; i += NT) cfma_cj(part, s_v[i], s_p[i]);
-      cplx<R> K = block_csum(part, red);
-      K = (beta * R(0.5)) * K;
-      for (int i = j + 1 + tid; i < n; i += NT) s_p[i] = s_p[i] - K * s_v[i];
-      __syncthreads();
-      // A_sub -= v w^H + w v^H
-      for (int64_t e = tid; e < (int64_t)(n - j - 1) * (n - j - 1); e += NT) {
-        int i = j + 1 + (int)(e % (n - j - 1)), c = j + 1 + (int)(e / (n - j - 1));
-        cplx<R> t = A[(int64_t)c * n + i];
-        t = t - s_v[i] * conjg(s_p[c]) - s_p[i] * conjg(s_v[c]);
-        A[(int64_t)c * n + i] = t;
+      R s = 0;
+      for (int i = j + 2 + tid; i < n; i += NT) s += norm2(col[i]);
+      s = block_sum(s, red);
+      const cplx<R> a = col[j + 1];
+      const R aa = sqrt(norm2(a));
+      const R nrm = sqrt(aa * aa + s);
+      const cplx<R> ph = (aa > R(0)) ? mk<R>(a.x / aa, a.y / aa) : mk<R>(1, 0);
+      const R beta = (nrm > tiny_norm<R>()) ? R(1) / (nrm * (nrm + aa)) : R(0);
+      const cplx<R> v0 = a + nrm * ph;
+      for (int i = tid; i < n; i += NT) {
+        const cplx<R> v = (i > j + 1) ? col[i] : (i == j + 1 ? v0 : mk<R>(0, 0));
+        s_v[i] = v;
+        Vb[jj * n + i] = v;
       }
+      if (tid == 0) s_beta[j] = beta;
+      __syncthreads();
+      if (beta != R(0)) {
+        // x1_l = w_l^H v, x2_l = v_l^H v for the panel's earlier reflectors
+        for (int d = wid; d < 2 * jj; d += NT / 32) {
+          const cplx<R>* u = (d < jj) ? Wb + d * n : Vb + (d - jj) * n;
+          cplx<R> acc = mk<R>(0, 0);
+          for (int i = j + 1 + lane; i < n; i += 32) cfma_cj(acc, u[i], s_v[i]);
+          for (int o = 16; o > 0; o >>= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+          }
+          if (lane == 0) s_x[d] = acc;
+        }
+        __syncthreads();
+        // p = beta (A_sub v - V x1 - W x2) on rows j+1..
+        for (int i = j + 1 + tid; i < n; i += NT) {
+          cplx<R> acc0 = mk<R>(0, 0), acc1 = mk<R>(0, 0);
+          int c = j + 1;
+          for (; c + 1 < n; c += 2) {
+            cfma(acc0, A[(int64_t)c * n + i], s_v[c]);
+            cfma(acc1, A[(int64_t)(c + 1) * n + i], s_v[c + 1]);
+          }
+          if (c < n) cfma(acc0, A[(int64_t)c * n + i], s_v[c]);
+          cplx<R> acc = acc0 + acc1;
+          for (int l = 0; l < jj; ++l) {
+            acc = acc - Vb[l * n + i] * s_x[l];
+            acc = acc - Wb[l * n + i] * s_x[jj + l];
+          }
+          s_p[i] = beta * acc;
+        }
+        __syncthreads();
+        // K = (beta / 2) v^H p ; w = p - K v
+        cplx<R> part = mk<R>(0, 0);
+        for (int i = j + 1 + tid; i < n; i += NT) cfma_cj(part, s_v[i], s_p[i]);
+        cplx<R> K = block_csum(part, red);
+        K = (beta * R(0.5)) * K;
+        for (int i = tid; i < n; i += NT) Wb[jj * n + i] = (i > j) ? s_p[i] - K * s_v[i] : mk<R>(0, 0);
+      } else {
+        for (int i = tid; i < n; i += NT) Wb[jj * n + i] = mk<R>(0, 0);
+      }
+      __syncthreads();
+      if (tid == 0) {
+        col[j + 1] = (beta != R(0)) ? mk<R>(-nrm * ph.x, -nrm * ph.y) : a;  // the new subdiagonal e_j
+        s_v0[j] = v0;  // v_{j+1}; v_i for i >= j + 2 stay in col[i]
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    if (tid == 0) {
-      col[j + 1] = (beta != R(0)) ? mk<R>(-nrm * ph.x, -nrm * ph.y) : a;  // the new subdiagonal e_j
-      s_v0[j] = v0;  // v_{j+1}; v_i for i >= j + 2 stay in col[i]
+    // trailing block (rows and columns from t0 on): A -= V W^H + W V^H over the panel
+    const int t0 = j0 + pb, nt = n - t0;
+    for (int64_t e = tid; e < (int64_t)nt * nt; e += NT) {
+      const int i = t0 + (int)(e % nt), c = t0 + (int)(e / nt);
+      cplx<R> v = A[(int64_t)c * n + i];
+      for (int l = 0; l < pb; ++l) {
+        v = v - Vb[l * n + i] * conjg(Wb[l * n + c]);
+        v = v - Wb[l * n + i] * conjg(Vb[l * n + c]);
+      }
+      A[(int64_t)c * n + i] = v;
     }
     __syncthreads();
   }
@@ -395,7 +449,16 @@ template <typename R>
 cudaError_t heevk(cudaStream_t s, int batch, const EigArgs<R>& g) {
   if (batch <= 0 || g.n <= 0 || g.k <= 0) return cudaSuccess;
   if (g.n > MAXN || g.k > g.n || g.k + 1 > MAXN / 2) return cudaErrorInvalidValue;
-  heevk_kernel<R><<<batch, NT, 0, s>>>(g);
+  constexpr int NB = sizeof(R) == 4 ? 16 : 8;  // reflectors per panel of the tridiagonalisation
+  const size_t bytes = 2 * sizeof(cplx<R>) * (size_t)NB * g.n;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(heevk_kernel<R, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(2 * sizeof(cplx<R>) * NB * MAXN));
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  heevk_kernel<R, NB><<<batch, NT, bytes, s>>>(g);
   return cudaGetLastError();
 }
 
