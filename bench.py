@@ -208,10 +208,19 @@ def per_update_error(st, r, prec):
     return {k: float(np.max(np.abs(rdm[k] - ref)) / nrm) for k in ("fp32", "mixed", "fp64_perturbed")}
 
 
+_T0 = time.perf_counter()
+
+
+def progress(msg):
+    """Phase timestamps on stderr (the JSON line alone goes to stdout)."""
+    print(f"[bench {time.perf_counter() - _T0:7.1f} s] {msg}", file=sys.stderr, flush=True)
+
+
 def run_ours(args, torch, rank, world):
     from paper_2508_07610_gb300 import build as Bld
 
     Bld.build()
+    progress("library built")
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream()
@@ -222,14 +231,18 @@ def run_ours(args, torch, rank, world):
     r = Runner(B, args.prec, sp, seed, depth, torch)
     st = r.st
     st.set_tensor_cores(args.tc)
+    progress("handle, channels and gates ready")
     # ---- reach the steady state: every bond at chi = 64 and every Kraus leg at kappa = 8
     for layer in range(args.saturate):
         r.layer(layer)
     st.sync()
     bonds, kraus = st.dims()
     assert min(bonds[4:-4]) == CHI and min(kraus) == KAPPA, (bonds, kraus)
+    progress("saturated")
     zz_fast = st.zz_map()[0]
+    progress("zz map read")
     upd_err = per_update_error(st, r, args.prec) if rank == 0 else None
+    progress("per-update accuracy measured")
     # ---- capture an even + odd layer pair (the last bond alternates between 16 and 64 with the
     # layer parity, so a pair maps the steady state onto itself); the graph puts the centre and the
     # site storage back where they were on exit so that it can be replayed
@@ -239,6 +252,7 @@ def run_ours(args, torch, rank, world):
     r.layer(1)
     graph = st.capture_end(restore=True)
     per_step = st.launch_count() - c0
+    progress("layer pair captured")
     n2q_step = (r.n2q(0) + r.n2q(1)) * B
     # ---- warm-up
     for s in range(args.warmup):
@@ -260,6 +274,7 @@ def run_ours(args, torch, rank, world):
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
     ms = ev0.elapsed_time(ev1)
+    progress("timed region done")
     barrier(torch, world)
     launches = per_step * args.steps
     ms_max = allreduce_max(torch, world, ms)
@@ -273,6 +288,7 @@ def run_ours(args, torch, rank, world):
     for s in range(2):
         r.layer(s)
     prof = st.profile_read()
+    progress("per-class profile read")
     st.profile(False)
     # ---- end-to-end through the C ABI from host buffers: H2D of the step's gate matrices from
     # pinned memory, the layer through the public calls, D2H of the step's result (discarded weights)
@@ -292,6 +308,7 @@ def run_ours(args, torch, rank, world):
         e2e_2q += r.n2q(s) * B
     t_e2e = time.perf_counter() - t0
     e2e_val = allreduce_sum(torch, world, e2e_2q) / allreduce_max(torch, world, t_e2e)
+    progress("end-to-end pass done")
     h2d = int(pinned[0].numel() * 16)
     d2h = 3 * 8 * B
     # ---- plain path: one chain, complex128, launch by launch
@@ -314,6 +331,7 @@ def run_ours(args, torch, rank, world):
         e1.record(stream)
         torch.cuda.synchronize()
         plain = cnt / (e0.elapsed_time(e1) / 1e3)
+        progress("plain complex128 chain done")
         del rp
     return {
         "value": value, "ms": ms_max, "n2q": total_2q, "disc": disc, "prof": prof, "e2e": e2e_val,

@@ -170,6 +170,8 @@ struct Eng : EngBase {
   int64_t sQR = 0, sE = 0, sT = 0, sZ = 0, sF = 0, sU = 0, sH = 0, sY = 0, sX = 0;
   CE *wF64 = nullptr, *wU64 = nullptr;
   ER *wEval = nullptr, *wScr = nullptr;
+  C* wSK = nullptr;
+  int64_t sSK = 0;
   int64_t sEval = 0, sScr = 0;
   double* dDisc = nullptr;  // [B][3]: chi, kappa, gap
   // readout buffers
@@ -181,7 +183,7 @@ struct Eng : EngBase {
   int64_t pCap = 0, pECap = 0, pLimit = 0;
 
   ~Eng() override {
-    void* ptrs[] = {pool, wQR, wQ, wE, wT, wZ, wF, wU, wH, wY, wX, wK, wRt, wF64, wU64, wEval, wScr, dDisc,
+    void* ptrs[] = {pool, wQR, wQ, wE, wT, wZ, wF, wU, wH, wY, wX, wK, wRt, wF64, wU64, wEval, wScr, dDisc, wSK,
                     envL, envR, tmpA, tmpB, dDot, pX, pP, pE, pE2, iota};
     for (void* p : ptrs)
       if (p) cudaFree(p);
@@ -237,6 +239,8 @@ struct Eng : EngBase {
     sScr = lmax(sScr, eig_scratch_elems(16, 16));
     CK(dmalloc(&wScr, sScr * B));
     CK(dmalloc(&dDisc, (int64_t)3 * B));
+    sSK = 4 * lmax(256 * K * K, 1024) * B;  // split-K partials of the long Gram products
+    CK(dmalloc(&wSK, sSK));
     sEnv = X * X;
     CK(dmalloc(&envL, sEnv * B * (n + 1)));
     CK(dmalloc(&envR, sEnv * B * (n + 1)));
@@ -283,6 +287,8 @@ struct Eng : EngBase {
     GemmArgs<R> g;
     g.herm = herm;
     g.allow_tc = tensor_cores ? 1 : 0;
+    g.ws = wSK;
+    g.ws_elems = sSK;
     g.M = M;
     g.N = N;
     g.K = K;

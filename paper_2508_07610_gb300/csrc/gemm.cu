@@ -13,6 +13,9 @@
 // Long FP32 reductions (K >= 1024, the Gram matrices of the truncations) sum each k-tile into a fresh
 // partial and add it to the running value with Knuth's TwoSum, so their rounding error does not grow
 // with K; the other products accumulate directly.
+// Long reductions whose output has too few tiles to fill the GPU (the Kraus-leg Grams: 128 x 128
+// or 32 x 32 per chain over 8192 rows) are split along K over several CTAs; each writes its partial
+// tile to a workspace and a second kernel adds the partials in FP64 and applies alpha and beta.
 #include "kernels.h"
 
 namespace mpdo {
@@ -55,7 +58,7 @@ constexpr size_t smem_bytes() {
 }
 
 template <typename R, bool COMP, int TMR, int TNC, int STAGES>
-__global__ void __launch_bounds__(NT, 2) gemm_kernel(GemmArgs<R> g, int a_m_fast, int b_n_fast) {
+__global__ void __launch_bounds__(NT, 2) gemm_kernel(GemmArgs<R> g, int a_m_fast, int b_n_fast, int sk, int kc) {
   constexpr int BM = 16 * TMR, BN = 16 * TNC, SA = BM + PAD, SB = BN + PAD;
   constexpr int LA = BM * BK / NT, LB = BN * BK / NT;  // elements each thread copies per k-tile
   static_assert(LA >= 1 && LB >= 1, "tile too small for the thread count");
@@ -65,7 +68,8 @@ __global__ void __launch_bounds__(NT, 2) gemm_kernel(GemmArgs<R> g, int a_m_fast
   int64_t* rowA = reinterpret_cast<int64_t*>(Bs + STAGES * BK * SB);  // [BM], -1 outside
   int64_t* colB = rowA + BM;                                          // [BN], -1 outside
 
-  const int z = blockIdx.z;
+  const int z = blockIdx.z / sk, kz = blockIdx.z % sk;  // batch item, K chunk
+  const int kb = kz * kc, ke = (g.K - kb < kc) ? g.K : kb + kc;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   if (g.herm && n0 > m0 + BM - 1) return;  // tile strictly above the diagonal of a Hermitian result
   const cplx<R>* A = g.A + view_batch(g.va, z);
@@ -88,7 +92,7 @@ __global__ void __launch_bounds__(NT, 2) gemm_kernel(GemmArgs<R> g, int a_m_fast
       const int ai = a_m_fast ? e % BM : e / BK, ak = a_m_fast ? e / BM : e % BK;
       const int k = k0 + ak;
       const int64_t ro = rowA[ai];
-      const bool ok = ro >= 0 && k < g.K;
+      const bool ok = ro >= 0 && k < ke;
       cp_elem(as + ak * SA + ai, ok ? A + ro + view_col(g.va, k) : A, ok);
     }
 #pragma unroll
@@ -97,7 +101,7 @@ __global__ void __launch_bounds__(NT, 2) gemm_kernel(GemmArgs<R> g, int a_m_fast
       const int bj = b_n_fast ? e % BN : e / BK, bk = b_n_fast ? e / BN : e % BK;
       const int k = k0 + bk;
       const int64_t co = colB[bj];
-      const bool ok = co >= 0 && k < g.K;
+      const bool ok = co >= 0 && k < ke;
       cp_elem(bs + bk * SB + bj, ok ? B + co + view_row(g.vb, k) : B, ok);
     }
   };
@@ -115,10 +119,10 @@ __global__ void __launch_bounds__(NT, 2) gemm_kernel(GemmArgs<R> g, int a_m_fast
   }
   const bool conjA = g.va.conj != 0, conjB = g.vb.conj != 0;
 
-  const int nk = (g.K + BK - 1) / BK;
+  const int nk = (ke - kb + BK - 1) / BK;
 #pragma unroll
   for (int s = 0; s < STAGES - 1; ++s) {
-    if (s < nk) load_tile(s, s * BK);
+    if (s < nk) load_tile(s, kb + s * BK);
     cp_commit();
   }
   for (int kt = 0; kt < nk; ++kt) {
@@ -126,7 +130,7 @@ __global__ void __launch_bounds__(NT, 2) gemm_kernel(GemmArgs<R> g, int a_m_fast
     __syncthreads();  // tile kt is in shared memory for every thread; stage (kt - 1) is free
     {
       const int pf = kt + STAGES - 1;
-      if (pf < nk) load_tile(pf % STAGES, pf * BK);
+      if (pf < nk) load_tile(pf % STAGES, kb + pf * BK);
       cp_commit();
     }
     const cplx<R>* as = As + (kt % STAGES) * BK * SA;
@@ -171,6 +175,23 @@ __global__ void __launch_bounds__(NT, 2) gemm_kernel(GemmArgs<R> g, int a_m_fast
   }
   cp_wait<0>();
 
+  if (sk > 1) {  // partial tile of K chunk kz -> workspace [z][kz][M][N]
+    cplx<R>* P = g.ws + ((int64_t)z * sk + kz) * g.M * g.N;
+#pragma unroll
+    for (int r = 0; r < TMR; ++r) {
+      const int i = m0 + ty * TMR + r;
+      if (i >= g.M) continue;
+#pragma unroll
+      for (int c = 0; c < TNC; ++c) {
+        const int j = n0 + tx + 16 * c;
+        if (j >= g.N) continue;
+        cplx<R> sum = acc[r][c];
+        if constexpr (COMP) sum = sum + comp[r][c];
+        P[(int64_t)i * g.N + j] = sum;
+      }
+    }
+    return;
+  }
   const bool use_beta = (g.beta.x != R(0) || g.beta.y != R(0));
 #pragma unroll
   for (int r = 0; r < TMR; ++r) {
@@ -196,6 +217,36 @@ __global__ void __launch_bounds__(NT, 2) gemm_kernel(GemmArgs<R> g, int a_m_fast
   }
 }
 
+// C = alpha * (sum of the sk partials, in FP64) + beta * C; Hermitian results only on and below the
+// diagonal (the caller mirrors the strict upper triangle)
+template <typename R>
+__global__ void splitk_reduce_kernel(GemmArgs<R> g, int sk) {
+  const int z = blockIdx.y;
+  const int64_t MN = (int64_t)g.M * g.N;
+  const cplx<R>* P = g.ws + (int64_t)z * sk * MN;
+  cplx<R>* C = g.C + view_batch(g.vc, z);
+  const bool use_beta = (g.beta.x != R(0) || g.beta.y != R(0));
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < MN; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / g.N), j = (int)(e % g.N);
+    if (g.herm && j > i) continue;
+    double sx = 0, sy = 0;
+    for (int t = 0; t < sk; ++t) {
+      const cplx<R> p = P[t * MN + e];
+      sx += (double)p.x;
+      sy += (double)p.y;
+    }
+    cplx<R> v = g.alpha * mk<R>((R)sx, (R)sy);
+    const int64_t o = view_row(g.vc, i) + view_col(g.vc, j);
+    if (use_beta) {
+      cplx<R> old = C[o];
+      if (g.vc.conj) old.y = -old.y;
+      v = v + g.beta * old;
+    }
+    if (g.vc.conj) v.y = -v.y;
+    C[o] = v;
+  }
+}
+
 template <typename R, bool COMP, int TMR, int TNC>
 cudaError_t launch(cudaStream_t s, int batch, const GemmArgs<R>& g) {
   constexpr int BM = 16 * TMR, BN = 16 * TNC;
@@ -203,16 +254,40 @@ cudaError_t launch(cudaStream_t s, int batch, const GemmArgs<R>& g) {
   constexpr int STAGES = sizeof(R) == 4 ? 3 : 2;
   constexpr size_t bytes = smem_bytes<R, TMR, TNC, STAGES>();
   static bool attr_set = false;
+  static int n_sm = 0;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(gemm_kernel<R, COMP, TMR, TNC, STAGES>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0) n_sm = 1;
     attr_set = true;
   }
   const int a_m_fast = (g.va.rdiv == 0 && g.va.rlo == 1) ? 1 : 0;
   const int b_n_fast = (g.vb.cdiv == 0 && g.vb.clo == 1) ? 1 : 0;
-  dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, batch);
-  gemm_kernel<R, COMP, TMR, TNC, STAGES><<<grid, NT, bytes, s>>>(g, a_m_fast, b_n_fast);
+  const int tm = (g.M + BM - 1) / BM, tn = (g.N + BN - 1) / BN;
+  // split K when the output tiles (on and below the diagonal for a Hermitian result) cannot keep
+  // two CTAs on every SM busy for four waves and each chunk still spans at least 64 k-tiles
+  int sk = 1;
+  if (g.ws && g.K >= 1024) {
+    const int64_t tiles = (int64_t)(g.herm ? tm * (tm + 1) / 2 : tm * tn) * batch;
+    const int64_t want = (8 * (int64_t)n_sm + tiles - 1) / tiles;
+    const int64_t most = g.K / (64 * BK);
+    sk = (int)(want < most ? want : most);
+    if (sk > 8) sk = 8;
+    while (sk > 1 && ((int64_t)sk * g.M * g.N * batch > g.ws_elems || (int64_t)sk * batch > 65535)) --sk;
+    if (sk < 1) sk = 1;
+  }
+  const int kc = (sk > 1) ? ((g.K + sk - 1) / sk + BK - 1) / BK * BK : (g.K > 0 ? g.K : 1);
+  if (sk > 1) sk = (g.K + kc - 1) / kc;
+  dim3 grid(tn, tm, batch * sk);
+  gemm_kernel<R, COMP, TMR, TNC, STAGES><<<grid, NT, bytes, s>>>(g, a_m_fast, b_n_fast, sk, kc);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || sk == 1) return e;
+  const int64_t mn = (int64_t)g.M * g.N;
+  dim3 rgrid((unsigned)((mn + 255) / 256 < 1024 ? (mn + 255) / 256 : 1024), batch);
+  splitk_reduce_kernel<R><<<rgrid, 256, 0, s>>>(g, sk);
   return cudaGetLastError();
 }
 }  // namespace

@@ -19,6 +19,10 @@ struct GemmArgs {
   View vc;  // M x N; vc.conj stores conj(result)
   int herm = 0;  // M == N and the result is Hermitian: only tiles on or below the diagonal are computed
   int allow_tc = 0;  // complex64 only: route to the tensor-core GEMM when the shape qualifies
+  // optional workspace for split-K partial products (long reductions with few output tiles);
+  // nullptr disables splitting
+  cplx<R>* ws = nullptr;
+  int64_t ws_elems = 0;
 };
 template <typename R>
 cudaError_t gemm(cudaStream_t s, int batch, const GemmArgs<R>& g);
