@@ -161,17 +161,21 @@ class Runner:
 
 def _pair_rdm(sites, q):
     """Reduced density matrix of qubits (q, q+1) of an MPDO with arbitrary gauge: transfer matrices
-    over the sites left and right of the pair (physical and Kraus legs traced), the pair contracted."""
+    over the sites left and right of the pair (physical and Kraus legs traced), the pair contracted.
+    Every step is a pairwise contraction (one BLAS product each)."""
+    def ein(spec, x, y):
+        return np.einsum(spec, x, y, optimize=True)
+
     L = np.ones((1, 1), dtype=np.complex128)
     for a in sites[:q]:
-        L = np.einsum("ab,apnr,bpns->rs", L, a, a.conj())
+        L = ein("bpnr,bpns->rs", ein("ab,apnr->bpnr", L, a), a.conj())
     R = np.ones((1, 1), dtype=np.complex128)
     for a in reversed(sites[q + 2:]):
-        R = np.einsum("apnr,bpns,rs->ab", a, a.conj(), R)
+        R = ein("apns,bpns->ab", ein("apnr,rs->apns", a, R), a.conj())
     a1, a2 = sites[q], sites[q + 1]
-    th = np.einsum("lxmb,bynr->lxymnr", a1, a2)
-    th = th.reshape(a1.shape[0], 4, -1, a2.shape[-1])
-    return np.einsum("ab,axkr,bykS,rS->xy", L, th, th.conj(), R)
+    th = ein("lxmb,bynr->lxymnr", a1, a2).reshape(a1.shape[0], 4, -1, a2.shape[-1])
+    X = ein("bxkr,rs->bxks", ein("ab,axkr->bxkr", L, th), R)
+    return ein("bxks,byks->xy", X, th.conj())
 
 
 def per_update_error(st, r, prec):
