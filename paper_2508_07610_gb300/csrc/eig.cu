@@ -15,6 +15,7 @@
 // (5) back-transformation through the phases and the Householder reflectors, one warp per vector.
 // Every loop is bounded; the input matrix is overwritten.
 #include "kernels.h"
+#include "panel.cuh"
 
 namespace mpdo {
 
@@ -73,7 +74,7 @@ __device__ int sturm_count(const R* d, const R* e2, int n, R sigma, R pivmin) {
 }
 
 template <typename R, int NB>
-__global__ void __launch_bounds__(NT) heevk_kernel(EigArgs<R> g) {
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) heevk_kernel(EigArgs<R> g) {
   __shared__ R red[NT / 32];
   __shared__ R s_d[MAXN], s_e2[MAXN], s_beta[MAXN];
   __shared__ cplx<R> s_p[MAXN], s_v[MAXN];
@@ -283,44 +284,99 @@ __global__ void __launch_bounds__(NT) heevk_kernel(EigArgs<R> g) {
       uint32_t h = hash32((uint32_t)(t * 7919 + 1) * 2654435761u ^ (uint32_t)(i * 40503 + 17));
       Zr[(int64_t)i * k + t] = R((int)(h >> 8) - (1 << 23)) / R(1 << 23);
     }
+    // the substitutions work through the vector in chunks of CH entries: the chunk's factors and
+    // inputs are loaded together (independent loads), then the recurrence runs on registers
+    constexpr int CH = 8;
     for (int it = 0; it < 3; ++it) {
       // forward: apply L^-1 with the row interchanges; zi is the running entry i
       R zi = Zr[t];
-      for (int i = 0; i + 1 < n; ++i) {
-        const int64_t o = (int64_t)i * k + t;
-        const R zn = Zr[o + k], f = Ldl[o];
-        if (Lpiv[o] != R(0)) {
-          Zr[o] = zn;
-          zi = zi - f * zn;
-        } else {
-          Zr[o] = zi;
-          zi = zn - f * zi;
+      for (int i0 = 0; i0 + 1 < n; i0 += CH) {
+        const int cnt = (n - 1 - i0 < CH) ? n - 1 - i0 : CH;
+        R zn[CH], f[CH], pv[CH], out[CH];
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+          if (c < cnt) {
+            const int64_t o = (int64_t)(i0 + c) * k + t;
+            zn[c] = Zr[o + k];
+            f[c] = Ldl[o];
+            pv[c] = Lpiv[o];
+          }
         }
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+          if (c < cnt) {
+            if (pv[c] != R(0)) {
+              out[c] = zn[c];
+              zi = zi - f[c] * zn[c];
+            } else {
+              out[c] = zi;
+              zi = zn[c] - f[c] * zi;
+            }
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+          if (c < cnt) Zr[(int64_t)(i0 + c) * k + t] = out[c];
       }
       Zr[(int64_t)(n - 1) * k + t] = zi;
       // backward: U z = y; z1, z2 are the solution entries i + 1, i + 2
       R zmax = 0, z1 = 0, z2 = 0;
-      for (int i = n - 1; i >= 0; --i) {
-        const int64_t o = (int64_t)i * k + t;
-        R v = Zr[o];
-        if (i + 1 < n) v -= Ldu[o] * z1;
-        if (i + 2 < n) v -= Ldu2[o] * z2;
-        v /= Ldd[o];
-        if (!(fabs(v) < R(1e30))) v = (v > 0) ? R(1e30) : R(-1e30);
-        Zr[o] = v;
-        zmax = fmax(zmax, fabs(v));
-        z2 = z1;
-        z1 = v;
+      for (int i1 = n - 1; i1 >= 0; i1 -= CH) {
+        const int cnt = (i1 + 1 < CH) ? i1 + 1 : CH;
+        R y[CH], du[CH], du2[CH], dd[CH];
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+          if (c < cnt) {
+            const int64_t o = (int64_t)(i1 - c) * k + t;
+            y[c] = Zr[o];
+            du[c] = Ldu[o];
+            du2[c] = Ldu2[o];
+            dd[c] = Ldd[o];
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+          if (c < cnt) {
+            const int i = i1 - c;
+            R v = y[c];
+            if (i + 1 < n) v -= du[c] * z1;
+            if (i + 2 < n) v -= du2[c] * z2;
+            v /= dd[c];
+            if (!(fabs(v) < R(1e30))) v = (v > 0) ? R(1e30) : R(-1e30);
+            y[c] = v;
+            zmax = fmax(zmax, fabs(v));
+            z2 = z1;
+            z1 = v;
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+          if (c < cnt) Zr[(int64_t)(i1 - c) * k + t] = y[c];
       }
-      R sc = (zmax > R(0)) ? R(1) / zmax : R(1);
+      const R sc = (zmax > R(0)) ? R(1) / zmax : R(1);
       R nn = 0;
-      for (int i = 0; i < n; ++i) {
-        R v = Zr[(int64_t)i * k + t] * sc;
-        Zr[(int64_t)i * k + t] = v;
-        nn += v * v;
+      for (int i0 = 0; i0 < n; i0 += CH) {
+        R y[CH];
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+          if (i0 + c < n) y[c] = Zr[(int64_t)(i0 + c) * k + t] * sc;
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+          if (i0 + c < n) nn += y[c] * y[c];
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+          if (i0 + c < n) Zr[(int64_t)(i0 + c) * k + t] = y[c];
       }
-      R inv = (nn > R(0)) ? R(1) / sqrt(nn) : R(0);
-      for (int i = 0; i < n; ++i) Zr[(int64_t)i * k + t] *= inv;
+      const R inv = (nn > R(0)) ? R(1) / sqrt(nn) : R(0);
+      for (int i0 = 0; i0 < n; i0 += CH) {
+        R y[CH];
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+          if (i0 + c < n) y[c] = Zr[(int64_t)(i0 + c) * k + t];
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+          if (i0 + c < n) Zr[(int64_t)(i0 + c) * k + t] = y[c] * inv;
+      }
     }
   }
   __syncthreads();
@@ -385,33 +441,60 @@ __global__ void __launch_bounds__(NT) heevk_kernel(EigArgs<R> g) {
     }
   }
 
-  // ---- (5) back-transformation u = H_0 ... H_{n-3} Phi z, one warp per vector
-  for (int t = wid; t < k; t += NT / 32) {
-    cplx<R>* u = U + (int64_t)t * n;
-    for (int i = lane; i < n; i += 32) u[i] = Zr[(int64_t)i * k + t] * PH[i];
-    __syncwarp();
-    for (int j = n - 3; j >= 0; --j) {
-      const R beta = s_beta[j];
-      if (beta == R(0)) continue;
-      const cplx<R>* col = A + (int64_t)j * n;  // v_i = col[i] for i >= j + 2, v_{j+1} = s_v0[j]
-      cplx<R> acc = mk<R>(0, 0);
-      for (int i = j + 1 + lane; i < n; i += 32) {
-        cplx<R> vi = (i == j + 1) ? s_v0[j] : col[i];
-        cfma_cj(acc, vi, u[i]);
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-      }
-      acc = beta * acc;
-      for (int i = j + 1 + lane; i < n; i += 32) {
-        cplx<R> vi = (i == j + 1) ? s_v0[j] : col[i];
-        u[i] = u[i] - vi * acc;
-      }
-      __syncwarp();
-    }
+  // ---- (5) back-transformation u = H_0 ... H_{n-3} Phi z for all k vectors at once, NB reflectors
+  // per panel (last panel first), each panel applied as one block reflector I - V T V^H
+  __shared__ cplx<R> s_T[NB * NB], s_S[NB * NB];
+  for (int64_t e = tid; e < (int64_t)n * k; e += NT) {
+    const int i = (int)(e % n), t = (int)(e / n);
+    U[e] = Zr[(int64_t)i * k + t] * PH[i];
   }
   __syncthreads();
+  const int nref = n - 2;  // reflectors H_0 .. H_{n-3}
+  for (int j0 = ((nref - 1) / NB) * NB; nref > 0 && j0 >= 0; j0 -= NB) {
+    const int pb = (nref - j0 < NB) ? nref - j0 : NB;
+    const int r0 = j0 + 1, M = n - r0;  // rows touched by the panel
+    // V panel: reflector j0 + l as column l (rows relative to r0): v_{j+1} = v0, v_i = A[j][i] below
+    for (int e = tid; e < pb * M; e += NT) {
+      const int l = e / M, r = e % M, i = r0 + r, j = j0 + l;
+      cplx<R> v = mk<R>(0, 0);
+      if (i == j + 1) v = s_v0[j];
+      else if (i > j + 1) v = A[(int64_t)j * n + i];
+      Vb[l * n + r] = v;
+    }
+    __syncthreads();
+    // T: S[l][m] = v_l^H v_m (l < m), T_mm = beta_m, T[0:m, m] = -beta_m T[0:m, 0:m] S[0:m, m]
+    for (int pr = wid; pr < pb * pb; pr += NT / 32) {
+      const int l = pr / pb, m = pr % pb;
+      if (l >= m) continue;
+      cplx<R> acc = mk<R>(0, 0);
+      for (int r = m + lane; r < M; r += 32) cfma_cj(acc, Vb[l * n + r], Vb[m * n + r]);
+      acc = panel::warp_csum(acc);
+      if (lane == 0) s_S[l * NB + m] = acc;
+    }
+    __syncthreads();
+    for (int m = 0; m < NB; ++m) {
+      if (tid < NB) {
+        const int l = tid;
+        cplx<R> tv = mk<R>(0, 0);
+        if (m < pb && l < m) {
+          cplx<R> acc = mk<R>(0, 0);
+          for (int q = l; q < m; ++q) cfma(acc, s_T[l + q * NB], s_S[q * NB + m]);
+          tv = -s_beta[j0 + m] * acc;
+        } else if (m < pb && l == m) {
+          tv = mk<R>(s_beta[j0 + m], 0);
+        }
+        s_T[l + m * NB] = tv;
+      }
+      __syncthreads();
+    }
+    // U[r0:, :] <- (I - V T V^H) U[r0:, :]
+    panel::panel_vh_times<R, NB>(U + r0, n, M, k, Vb, n, pb, Wb, n);
+    __syncthreads();
+    panel::panel_apply_t<R, NB>(s_T, pb, false, Wb, n, k);
+    __syncthreads();
+    panel::panel_minus_v_times<R, NB>(U + r0, n, M, k, Vb, n, pb, Wb, n);
+    __syncthreads();
+  }
 
   // ---- outputs
   cplx<R>* V = g.V + view_batch(g.vv, z);
@@ -449,7 +532,7 @@ template <typename R>
 cudaError_t heevk(cudaStream_t s, int batch, const EigArgs<R>& g) {
   if (batch <= 0 || g.n <= 0 || g.k <= 0) return cudaSuccess;
   if (g.n > MAXN || g.k > g.n || g.k + 1 > MAXN / 2) return cudaErrorInvalidValue;
-  constexpr int NB = sizeof(R) == 4 ? 16 : 8;  // reflectors per panel of the tridiagonalisation
+  constexpr int NB = 8;  // reflectors per panel (tridiagonalisation and back-transformation)
   const size_t bytes = 2 * sizeof(cplx<R>) * (size_t)NB * g.n;
   static bool attr_set = false;
   if (!attr_set) {

@@ -9,6 +9,7 @@
 #include <cooperative_groups.h>
 
 #include "kernels.h"
+#include "panel.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -326,101 +327,6 @@ __global__ void __launch_bounds__(NT) qr_cluster_kernel(QrArgs<R> g, int C, int 
 // reflectors instead of one and runs as two small matrix products with V in shared memory.  Q is
 // accumulated the same way, panels last to first.
 //
-// Ws[i * ldw + c] = (V^H A)[i][c] over a block of columns, A column-major (ld lda, rows 0..M-1 of
-// the block), V = the panel's pb reflectors in shared memory (column i at Vs + i * ldv).
-template <typename R, int NB>
-__device__ void panel_vh_times(const cplx<R>* A, int64_t lda, int M, int nc, const cplx<R>* Vs, int ldv, int pb,
-                               cplx<R>* Ws, int ldw) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int c0 = 2 * wid; c0 < nc; c0 += 2 * (NT / 32)) {
-    const bool two = c0 + 1 < nc;
-    cplx<R> acc0[NB], acc1[NB];
-#pragma unroll
-    for (int i = 0; i < NB; ++i) acc0[i] = acc1[i] = mk<R>(0, 0);
-    const cplx<R>* a0p = A + (int64_t)c0 * lda;
-    const cplx<R>* a1p = a0p + lda;
-    for (int r = lane; r < M; r += 32) {
-      const cplx<R> a0 = a0p[r];
-      const cplx<R> a1 = two ? a1p[r] : mk<R>(0, 0);
-#pragma unroll
-      for (int i = 0; i < NB; ++i) {
-        if (i < pb) {
-          const cplx<R> v = Vs[i * ldv + r];
-          cfma_cj(acc0[i], v, a0);
-          cfma_cj(acc1[i], v, a1);
-        }
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < NB; ++i) {
-      if (i < pb) {
-        const cplx<R> s0 = warp_csum(acc0[i]);
-        const cplx<R> s1 = warp_csum(acc1[i]);
-        if (lane == 0) {
-          Ws[i * ldw + c0] = s0;
-          if (two) Ws[i * ldw + c0 + 1] = s1;
-        }
-      }
-    }
-  }
-}
-
-// A -= V Y over a block of columns, Y[i][c] = Ws[i * ldw + c].
-template <typename R, int NB>
-__device__ void panel_minus_v_times(cplx<R>* A, int64_t lda, int M, int nc, const cplx<R>* Vs, int ldv, int pb,
-                                    const cplx<R>* Ws, int ldw) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int c0 = 2 * wid; c0 < nc; c0 += 2 * (NT / 32)) {
-    const bool two = c0 + 1 < nc;
-    cplx<R> y0[NB], y1[NB];
-#pragma unroll
-    for (int i = 0; i < NB; ++i) {
-      y0[i] = (i < pb) ? Ws[i * ldw + c0] : mk<R>(0, 0);
-      y1[i] = (i < pb && two) ? Ws[i * ldw + c0 + 1] : mk<R>(0, 0);
-    }
-    cplx<R>* a0p = A + (int64_t)c0 * lda;
-    cplx<R>* a1p = a0p + lda;
-    for (int r = lane; r < M; r += 32) {
-      cplx<R> s0 = mk<R>(0, 0), s1 = mk<R>(0, 0);
-#pragma unroll
-      for (int i = 0; i < NB; ++i) {
-        if (i < pb) {
-          const cplx<R> v = Vs[i * ldv + r];
-          cfma(s0, v, y0[i]);
-          cfma(s1, v, y1[i]);
-        }
-      }
-      a0p[r] = a0p[r] - s0;
-      if (two) a1p[r] = a1p[r] - s1;
-    }
-  }
-}
-
-// Ws[., c] <- T^H Ws[., c] (herm) or T Ws[., c]; T upper triangular pb x pb, column-major, ld NB
-template <typename R, int NB>
-__device__ void panel_apply_t(const cplx<R>* T, int pb, bool herm, cplx<R>* Ws, int ldw, int nc) {
-  for (int c = threadIdx.x; c < nc; c += NT) {
-    cplx<R> w[NB], y[NB];
-#pragma unroll
-    for (int i = 0; i < NB; ++i) w[i] = (i < pb) ? Ws[i * ldw + c] : mk<R>(0, 0);
-#pragma unroll
-    for (int i = 0; i < NB; ++i) {
-      cplx<R> acc = mk<R>(0, 0);
-      if (herm) {
-#pragma unroll
-        for (int k = 0; k <= i; ++k) cfma_cj(acc, T[k + i * NB], w[k]);  // (T^H)[i][k] = conj(T[k][i])
-      } else {
-#pragma unroll
-        for (int k = i; k < NB; ++k) cfma(acc, T[i + k * NB], w[k]);
-      }
-      y[i] = acc;
-    }
-#pragma unroll
-    for (int i = 0; i < NB; ++i)
-      if (i < pb) Ws[i * ldw + c] = y[i];
-  }
-}
-
 template <typename R, int NB>
 size_t blocked_smem_bytes(int m, int n) {
   const int x = m < n ? m : n;
@@ -536,11 +442,11 @@ __global__ void __launch_bounds__(NT) qr_blocked_kernel(QrArgs<R> g) {
     const int nc = n - p0 - pb;
     if (nc > 0) {
       cplx<R>* A = W + (int64_t)(p0 + pb) * m + p0;
-      panel_vh_times<R, NB>(A, m, M, nc, Vs, m, pb, Ws, n);
+      panel::panel_vh_times<R, NB>(A, m, M, nc, Vs, m, pb, Ws, n);
       __syncthreads();
-      panel_apply_t<R, NB>(T, pb, true, Ws, n, nc);
+      panel::panel_apply_t<R, NB>(T, pb, true, Ws, n, nc);
       __syncthreads();
-      panel_minus_v_times<R, NB>(A, m, M, nc, Vs, m, pb, Ws, n);
+      panel::panel_minus_v_times<R, NB>(A, m, M, nc, Vs, m, pb, Ws, n);
       __syncthreads();
     }
   }
@@ -563,11 +469,11 @@ __global__ void __launch_bounds__(NT) qr_blocked_kernel(QrArgs<R> g) {
     __syncthreads();
     const int nc = x - p0;
     cplx<R>* A = Q + (int64_t)p0 * m + p0;
-    panel_vh_times<R, NB>(A, m, M, nc, Vs, m, pb, Ws, n);
+    panel::panel_vh_times<R, NB>(A, m, M, nc, Vs, m, pb, Ws, n);
     __syncthreads();
-    panel_apply_t<R, NB>(Ts + (size_t)P * NB * NB, pb, false, Ws, n, nc);
+    panel::panel_apply_t<R, NB>(Ts + (size_t)P * NB * NB, pb, false, Ws, n, nc);
     __syncthreads();
-    panel_minus_v_times<R, NB>(A, m, M, nc, Vs, m, pb, Ws, n);
+    panel::panel_minus_v_times<R, NB>(A, m, M, nc, Vs, m, pb, Ws, n);
     __syncthreads();
   }
   // R: clear the reflectors below the diagonal of the leading x rows.
@@ -648,10 +554,13 @@ cudaError_t qr(cudaStream_t s, int batch, const QrArgs<R>& g) {
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
   }
-  // many matrices: the blocked kernel with the widest panel whose shared memory fits
-  constexpr size_t kBlockedBudget = 200 * 1024;
+  // many matrices: the blocked kernel with the widest panel that still lets two CTAs share an SM,
+  // else the widest panel that fits at all
+  constexpr size_t kBlockedBudget = 200 * 1024, kTwoPerSm = 110 * 1024;
   constexpr int NB1 = sizeof(R) == 4 ? 16 : 8, NB2 = NB1 / 2;
   const size_t b1 = blocked_smem_bytes<R, NB1>(g.m, g.n), b2 = blocked_smem_bytes<R, NB2>(g.m, g.n);
+  if (b1 <= kTwoPerSm) return launch_blocked<R, NB1>(s, batch, g, b1);
+  if (b2 <= kTwoPerSm) return launch_blocked<R, NB2>(s, batch, g, b2);
   if (b1 <= kBlockedBudget) return launch_blocked<R, NB1>(s, batch, g, b1);
   if (b2 <= kBlockedBudget) return launch_blocked<R, NB2>(s, batch, g, b2);
   qr_kernel<R><<<batch, NT, 0, s>>>(g);
