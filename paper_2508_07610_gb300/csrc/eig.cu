@@ -22,6 +22,7 @@ namespace mpdo {
 namespace {
 constexpr int NT = 256;
 constexpr int MAXN = 512;
+constexpr int GB = 8;  // vectors per block of the Gram-Schmidt step
 
 template <typename R>
 __device__ R block_sum(R v, R* red) {
@@ -381,12 +382,41 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) heevk_kernel(EigAr
   }
   __syncthreads();
 
-  // ---- (4) Gram-Schmidt (twice) in descending order; redo a vector that collapses
-  for (int t = 0; t < k; ++t) {
+  // ---- (4) Gram-Schmidt (twice) in descending order, in blocks of GB vectors: each block is first
+  // projected against every earlier vector as a block (twice), then orthogonalised within itself
+  // vector by vector; a vector that collapses is redone from a fresh start against all earlier ones
+  R* s_G = reinterpret_cast<R*>(Wb + (size_t)NB * n);  // GB x k: the block's projections (dynamic)
+  for (int t0 = 0; t0 < k; t0 += GB) {
+  const int nb = (k - t0 < GB) ? k - t0 : GB;
+  if (t0 > 0) {
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int e = tid; e < t0 * nb; e += NT) {
+        const int u = e % t0, c = e / t0;
+        R acc0 = 0, acc1 = 0;
+        int i = 0;
+        for (; i + 1 < n; i += 2) {
+          acc0 += Zr[(int64_t)i * k + u] * Zr[(int64_t)i * k + t0 + c];
+          acc1 += Zr[(int64_t)(i + 1) * k + u] * Zr[(int64_t)(i + 1) * k + t0 + c];
+        }
+        if (i < n) acc0 += Zr[(int64_t)i * k + u] * Zr[(int64_t)i * k + t0 + c];
+        s_G[c * k + u] = acc0 + acc1;
+      }
+      __syncthreads();
+      for (int e = tid; e < n * nb; e += NT) {
+        const int c = e % nb, i = e / nb;
+        R v = Zr[(int64_t)i * k + t0 + c];
+        for (int u = 0; u < t0; ++u) v -= s_G[c * k + u] * Zr[(int64_t)i * k + u];
+        Zr[(int64_t)i * k + t0 + c] = v;
+      }
+      __syncthreads();
+    }
+  }
+  for (int t = t0; t < t0 + nb; ++t) {
     for (int attempt = 0; attempt < 3; ++attempt) {
+      const int ub = (attempt == 0) ? t0 : 0;  // earlier blocks were projected out already
       for (int pass = 0; pass < 2; ++pass) {
-        // dots with all previous vectors: warp w handles previous vectors u = w, w + 8, ...
-        for (int u = wid; u < t; u += NT / 32) {
+        // dots with the previous vectors: warp w handles u = ub + w, ub + w + 8, ...
+        for (int u = ub + wid; u < t; u += NT / 32) {
           R acc = 0;
           for (int i = lane; i < n; i += 32) acc += Zr[(int64_t)i * k + u] * Zr[(int64_t)i * k + t];
           for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -395,7 +425,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) heevk_kernel(EigAr
         __syncthreads();
         for (int i = tid; i < n; i += NT) {
           R v = Zr[(int64_t)i * k + t];
-          for (int u = 0; u < t; ++u) v -= s_w[MAXN - 1 - u] * Zr[(int64_t)i * k + u];
+          for (int u = ub; u < t; ++u) v -= s_w[MAXN - 1 - u] * Zr[(int64_t)i * k + u];
           Zr[(int64_t)i * k + t] = v;
         }
         __syncthreads();
@@ -439,6 +469,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) heevk_kernel(EigAr
       }
       __syncthreads();
     }
+  }
   }
 
   // ---- (5) back-transformation u = H_0 ... H_{n-3} Phi z for all k vectors at once, NB reflectors
@@ -533,11 +564,11 @@ cudaError_t heevk(cudaStream_t s, int batch, const EigArgs<R>& g) {
   if (batch <= 0 || g.n <= 0 || g.k <= 0) return cudaSuccess;
   if (g.n > MAXN || g.k > g.n || g.k + 1 > MAXN / 2) return cudaErrorInvalidValue;
   constexpr int NB = 8;  // reflectors per panel (tridiagonalisation and back-transformation)
-  const size_t bytes = 2 * sizeof(cplx<R>) * (size_t)NB * g.n;
+  const size_t bytes = 2 * sizeof(cplx<R>) * (size_t)NB * g.n + sizeof(R) * (size_t)GB * g.k;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(heevk_kernel<R, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(2 * sizeof(cplx<R>) * NB * MAXN));
+                                         (int)(2 * sizeof(cplx<R>) * NB * MAXN + sizeof(R) * GB * (MAXN / 2)));
     if (e != cudaSuccess) return e;
     attr_set = true;
   }

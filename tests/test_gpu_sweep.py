@@ -31,8 +31,10 @@ def _compare(st, o, prec, label):
     print(f"sweep {label} {prec}: lim {lim:.2e} " + " ".join(f"{k}={v:.2e}" for k, v in {**errs, **derr}.items()))
     for k, v in errs.items():
         assert v < lim, (k, v, lim)
+    # a cut inside a near-degenerate cluster keeps one of several equally valid subspaces, and the later
+    # truncations' discarded weights depend on which: the same allowance as the readouts
     for k, v in derr.items():
-        assert v < dtol, (k, v, dtol)
+        assert v < dtol + 4 * o.cut_sensitivity(eps), (k, v, dtol)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed", "fp32"])
