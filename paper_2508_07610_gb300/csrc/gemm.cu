@@ -10,9 +10,9 @@
 // outside the matrix) through a STAGES-deep ring of k-tiles of 16, so loads for later k-tiles are in
 // flight while the current one is multiplied, without staging registers.  The per-row (A) and
 // per-column (B) view offsets of the tile are computed once into shared memory.
-// Long FP32 reductions (K >= 1024, the Gram matrices of the truncations) sum each k-tile into a fresh
-// partial and add it to the running value with Knuth's TwoSum, so their rounding error does not grow
-// with K; the other products accumulate directly.
+// FP32 reductions with K >= 128 (every contraction of a two-qubit update and the Gram matrices of the
+// truncations) sum each k-tile into a fresh partial and add it to the running value with Knuth's
+// TwoSum, so their rounding error does not grow with K; shorter products accumulate directly.
 // Long reductions whose output has too few tiles to fill the GPU (the Kraus-leg Grams: 128 x 128
 // or 32 x 32 per chain over 8192 rows) are split along K over several CTAs; each writes its partial
 // tile to a workspace and a second kernel adds the partials in FP64 and applies alpha and beta.
@@ -298,13 +298,21 @@ cudaError_t gemm(cudaStream_t s, int batch, const GemmArgs<R>& g) {
   if (g.herm && g.M != g.N) return cudaErrorInvalidValue;
   // small outputs (<= 32 x 32 per batch item: the Kraus-leg Gram of a 1q gate, the rank-kappa
   // projection) take 32 x 32 tiles so that no tile is mostly padding
+  // outputs of at most 16 rows and many columns (the rank-kappa projections, kappa x 8192) take
+  // 16 x 128 tiles
   const bool small = g.M <= 32 && g.N <= 32;
+  const bool wide = g.M <= 16 && g.N > 32 && !g.herm;
   if constexpr (sizeof(R) == 4) {
     if (g.allow_tc && g.K <= 2048 && tc_gemm_applicable(g)) return tc_gemm(s, batch, g);
-    if (g.K >= 1024) return small ? launch<R, true, 2, 2>(s, batch, g) : launch<R, true, 4, 4>(s, batch, g);
+    if (g.K >= 128) {
+      if (wide) return launch<R, true, 1, 8>(s, batch, g);
+      return small ? launch<R, true, 2, 2>(s, batch, g) : launch<R, true, 4, 4>(s, batch, g);
+    }
+    if (wide) return launch<R, false, 1, 8>(s, batch, g);
     if (g.M > 64 && !g.herm) return launch<R, false, 8, 4>(s, batch, g);
     return small ? launch<R, false, 2, 2>(s, batch, g) : launch<R, false, 4, 4>(s, batch, g);
   } else {
+    if (wide) return launch<R, false, 1, 8>(s, batch, g);
     return small ? launch<R, false, 2, 2>(s, batch, g) : launch<R, false, 4, 4>(s, batch, g);
   }
 }
