@@ -227,54 +227,72 @@ def run_ours(args, torch, rank, world):
     progress("library built")
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    stream = torch.cuda.Stream()
-    sp = stream.cuda_stream
     B = args.chains
+    G = max(1, args.groups)
+    if B % G:
+        raise SystemExit(f"--chains {B} is not a multiple of --groups {G}")
+    Bg = B // G
     depth = 2
     seed = 0x2508076100 + 2 + 1000 * rank
-    r = Runner(B, args.prec, sp, seed, depth, torch)
-    st = r.st
-    st.set_tensor_cores(args.tc)
-    progress("handle, channels and gates ready")
+    # G handles of B / G chains, each on its own stream: their launches overlap on the GPU, so one
+    # group's matrix products fill the SMs while another runs its latency-bound factorisations
+    streams = [torch.cuda.Stream() for _ in range(G)]
+    runners = [Runner(Bg, args.prec, streams[g].cuda_stream, seed + 7919 * g, depth, torch) for g in range(G)]
+    r, st, stream = runners[0], runners[0].st, streams[0]
+    for rg in runners:
+        rg.st.set_tensor_cores(args.tc)
+    progress("handles, channels and gates ready")
     # ---- reach the steady state: every bond at chi = 64 and every Kraus leg at kappa = 8
     for layer in range(args.saturate):
-        r.layer(layer)
-    st.sync()
-    bonds, kraus = st.dims()
-    assert min(bonds[4:-4]) == CHI and min(kraus) == KAPPA, (bonds, kraus)
+        for rg in runners:
+            rg.layer(layer)
+    for rg in runners:
+        rg.st.sync()
+        bonds, kraus = rg.st.dims()
+        assert min(bonds[4:-4]) == CHI and min(kraus) == KAPPA, (bonds, kraus)
     progress("saturated")
     zz_fast = st.zz_map()[0]
     progress("zz map read")
     upd_err = per_update_error(st, r, args.prec) if rank == 0 else None
     progress("per-update accuracy measured")
-    # ---- capture an even + odd layer pair (the last bond alternates between 16 and 64 with the
-    # layer parity, so a pair maps the steady state onto itself); the graph puts the centre and the
-    # site storage back where they were on exit so that it can be replayed
-    c0 = st.launch_count()
-    st.capture_begin()
-    r.layer(0)
-    r.layer(1)
-    graph = st.capture_end(restore=True)
-    per_step = st.launch_count() - c0
-    progress("layer pair captured")
+    # ---- capture an even + odd layer pair per group (the last bond alternates between 16 and 64
+    # with the layer parity, so a pair maps the steady state onto itself); each graph puts the centre
+    # and the site storage back where they were on exit so that it can be replayed
+    graphs, per_step = [], 0
+    for rg in runners:
+        c0 = rg.st.launch_count()
+        rg.st.capture_begin()
+        rg.layer(0)
+        rg.layer(1)
+        graphs.append(rg.st.capture_end(restore=True))
+        per_step += rg.st.launch_count() - c0
+    progress("layer pairs captured")
     n2q_step = (r.n2q(0) + r.n2q(1)) * B
     # ---- warm-up
     for s in range(args.warmup):
-        graph.launch()
-    st.sync()
-    lc0 = st.launch_count()
-    # ---- timed region
+        for gr in graphs:
+            gr.launch()
+    torch.cuda.synchronize()
+    # ---- timed region: events on a join stream that every group stream waits for and joins back
+    join = torch.cuda.Stream()
     barrier(torch, world)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     n2q = 0
     with ClockSampler(dev.index) as clk:
         torch.cuda.nvtx.range_push("timed")
-        ev0.record(stream)
+        ev0.record(join)
+        for sg in streams:
+            sg.wait_event(ev0)
         for s in range(args.steps):
-            graph.launch()
+            for gr in graphs:
+                gr.launch()
             n2q += n2q_step
-        ev1.record(stream)
+        for sg in streams:
+            done = torch.cuda.Event()
+            done.record(sg)
+            join.wait_event(done)
+        ev1.record(join)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
     ms = ev0.elapsed_time(ev1)
@@ -284,43 +302,46 @@ def run_ours(args, torch, rank, world):
     ms_max = allreduce_max(torch, world, ms)
     total_2q = allreduce_sum(torch, world, n2q)
     value = total_2q / (ms_max / 1e3)
-    # ---- accuracy check of the steady-state mixed path: one more layer on a 1-chain FP64 twin
-    # is done in the tests; here report the discarded weights and a readout for context
     disc = st.discarded()
-    # ---- per-kernel-class timing of the same layers (CUDA events around every launch, no graph)
+    # ---- per-kernel-class timing of the same layers on group 0 alone (CUDA events around every
+    # launch, no graph, no other group running)
     st.profile(True)
     for s in range(2):
         r.layer(s)
     prof = st.profile_read()
     progress("per-class profile read")
     st.profile(False)
-    # ---- end-to-end through the C ABI from host buffers: H2D of the step's gate matrices from
-    # pinned memory, the layer through the public calls, D2H of the step's result (discarded weights)
-    pinned = torch.empty(r.U1.shape, dtype=torch.complex128, pin_memory=True)
-    pinned.copy_(torch.from_numpy(r.U1_host))
-    Udev = torch.empty_like(r.U1)
+    # ---- end-to-end through the C ABI from host buffers: per step and group, H2D of the step's gate
+    # matrices from pinned memory, the layer through the public calls, D2H of the step's result
+    # (discarded weights)
+    pinned = [torch.empty(rg.U1.shape, dtype=torch.complex128, pin_memory=True) for rg in runners]
+    for pg, rg in zip(pinned, runners):
+        pg.copy_(torch.from_numpy(rg.U1_host))
+    Udev = [torch.empty_like(rg.U1) for rg in runners]
     e2e_steps = 2 * max(1, min(args.steps, 3))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e2e_2q = 0
     for s in range(e2e_steps):
         li = s % depth
-        with torch.cuda.stream(stream):
-            Udev[li].copy_(pinned[li], non_blocking=True)
-        r.layer(s, U1=Udev)
-        _ = st.discarded()
+        for g, rg in enumerate(runners):
+            with torch.cuda.stream(streams[g]):
+                Udev[g][li].copy_(pinned[g][li], non_blocking=True)
+            rg.layer(s, U1=Udev[g])
+        for rg in runners:
+            _ = rg.st.discarded()
         e2e_2q += r.n2q(s) * B
     t_e2e = time.perf_counter() - t0
     e2e_val = allreduce_sum(torch, world, e2e_2q) / allreduce_max(torch, world, t_e2e)
     progress("end-to-end pass done")
-    h2d = int(pinned[0].numel() * 16)
+    h2d = int(sum(pg[0].numel() for pg in pinned) * 16)
     d2h = 3 * 8 * B
     # ---- plain path: one chain, complex128, launch by launch
     plain = None
     err = None
     if rank == 0 and args.plain_steps > 0:
-        # the same gates and channels as chain 0 of the batch, in complex128 with FP64 eigensolvers
-        rp = Runner(1, "fp64", sp, seed, depth, torch)
+        # the same gates and channels as chain 0 of group 0, in complex128 with FP64 eigensolvers
+        rp = Runner(1, "fp64", stream.cuda_stream, seed, depth, torch)
         for layer in range(args.saturate):
             rp.layer(layer)
         rp.st.sync()
@@ -340,7 +361,7 @@ def run_ours(args, torch, rank, world):
     return {
         "value": value, "ms": ms_max, "n2q": total_2q, "disc": disc, "prof": prof, "e2e": e2e_val,
         "h2d": h2d, "d2h": d2h, "clocks": clk.summary(), "plain": plain,
-        "launches": launches, "B": B, "err": err, "upd_err": upd_err,
+        "launches": launches, "B": B, "G": G, "err": err, "upd_err": upd_err,
     }
 
 
@@ -499,6 +520,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--chains", type=int, default=256)
+    ap.add_argument("--groups", type=int, default=2, help="handles (streams) the chains are split over")
     ap.add_argument("--saturate", type=int, default=12)
     ap.add_argument("--plain-steps", type=int, default=1)
     ap.add_argument("--cpu-updates", type=int, default=1)
@@ -598,6 +620,8 @@ def main():
     roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
                 "ms_per_step_in_kernel": ms_d, "launches_per_step": cnt_d,
+                "measured_on": f"group 0 alone ({res['B'] // res['G']} chains), two uncaptured layers, CUDA events "
+                               "around every launch",
                 "peak_source": (f"FP32 FMA pipe from unit counts x {mhz:.0f} MHz (the measured-peaks file has "
                                 f"copy bandwidth and bf16 GEMM only)") if peak != 1.25 else
                                "nominal GB300 FP64 rate (no measured FP64 peak)",
@@ -615,7 +639,7 @@ def main():
                    "sample": f"failed: {e}"}
     prec_desc = {"mixed": "complex64 contractions, FP64 eigensolvers (MIXED)",
                  "fp32": "complex64 contractions, FP32 eigensolvers", "fp64": "complex128, FP64 eigensolvers"}
-    cfg.update({"chains_per_gpu": res["B"], "precision": prec_desc[args.prec],
+    cfg.update({"chains_per_gpu": res["B"], "concurrent_groups": res["G"], "precision": prec_desc[args.prec],
                 "per_update_rdm_err_vs_fp64": res["upd_err"][args.prec] if args.prec != "fp64" else 0.0,
                 "per_update_rdm_err_all_modes": res["upd_err"],
                 "max_abs_zz_err_vs_fp64_after_saturation": res["err"],
