@@ -519,8 +519,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--chains", type=int, default=256)
-    ap.add_argument("--groups", type=int, default=2, help="handles (streams) the chains are split over")
+    ap.add_argument("--chains", type=int, default=512)
+    ap.add_argument("--groups", type=int, default=4, help="handles (streams) the chains are split over")
     ap.add_argument("--saturate", type=int, default=12)
     ap.add_argument("--plain-steps", type=int, default=1)
     ap.add_argument("--cpu-updates", type=int, default=1)

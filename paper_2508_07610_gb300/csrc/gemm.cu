@@ -58,7 +58,8 @@ constexpr size_t smem_bytes() {
 }
 
 template <typename R, bool COMP, int TMR, int TNC, int STAGES>
-__global__ void __launch_bounds__(NT, 2) gemm_kernel(GemmArgs<R> g, int a_m_fast, int b_n_fast, int sk, int kc) {
+__global__ void __launch_bounds__(NT, 2) gemm_kernel(GemmArgs<R> g, int a_m_fast, int b_n_fast, int sk, int kc,
+                                                     int ty0) {
   constexpr int BM = 16 * TMR, BN = 16 * TNC, SA = BM + PAD, SB = BN + PAD;
   constexpr int LA = BM * BK / NT, LB = BN * BK / NT;  // elements each thread copies per k-tile
   static_assert(LA >= 1 && LB >= 1, "tile too small for the thread count");
@@ -70,7 +71,7 @@ __global__ void __launch_bounds__(NT, 2) gemm_kernel(GemmArgs<R> g, int a_m_fast
 
   const int z = blockIdx.z / sk, kz = blockIdx.z % sk;  // batch item, K chunk
   const int kb = kz * kc, ke = (g.K - kb < kc) ? g.K : kb + kc;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int m0 = (blockIdx.y + ty0) * BM, n0 = blockIdx.x * BN;  // ty0: row-tile offset of this launch
   if (g.herm && n0 > m0 + BM - 1) return;  // tile strictly above the diagonal of a Hermitian result
   const cplx<R>* A = g.A + view_batch(g.va, z);
   const cplx<R>* B = g.B + view_batch(g.vb, z);
@@ -281,10 +282,17 @@ cudaError_t launch(cudaStream_t s, int batch, const GemmArgs<R>& g) {
   }
   const int kc = (sk > 1) ? ((g.K + sk - 1) / sk + BK - 1) / BK * BK : (g.K > 0 ? g.K : 1);
   if (sk > 1) sk = (g.K + kc - 1) / kc;
-  dim3 grid(tn, tm, batch * sk);
-  gemm_kernel<R, COMP, TMR, TNC, STAGES><<<grid, NT, bytes, s>>>(g, a_m_fast, b_n_fast, sk, kc);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || sk == 1) return e;
+  // grid.y is limited to 65535 row tiles per launch: taller outputs (the purity contraction) take
+  // several launches over consecutive row-tile ranges
+  constexpr int kMaxY = 65535;
+  cudaError_t e = cudaSuccess;
+  for (int ty0 = 0; ty0 < tm; ty0 += kMaxY) {
+    dim3 grid(tn, (tm - ty0 < kMaxY) ? tm - ty0 : kMaxY, batch * sk);
+    gemm_kernel<R, COMP, TMR, TNC, STAGES><<<grid, NT, bytes, s>>>(g, a_m_fast, b_n_fast, sk, kc, ty0);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (sk == 1) return e;
   const int64_t mn = (int64_t)g.M * g.N;
   dim3 rgrid((unsigned)((mn + 255) / 256 < 1024 ? (mn + 255) / 256 : 1024), batch);
   splitk_reduce_kernel<R><<<rgrid, 256, 0, s>>>(g, sk);

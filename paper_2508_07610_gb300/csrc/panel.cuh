@@ -31,6 +31,7 @@ __device__ void panel_vh_times(const cplx<R>* A, int64_t lda, int M, int nc, con
     for (int i = 0; i < NB; ++i) acc0[i] = acc1[i] = mk<R>(0, 0);
     const cplx<R>* a0p = A + (int64_t)c0 * lda;
     const cplx<R>* a1p = a0p + lda;
+#pragma unroll 4
     for (int r = lane; r < M; r += 32) {
       const cplx<R> a0 = a0p[r];
       const cplx<R> a1 = two ? a1p[r] : mk<R>(0, 0);
@@ -72,6 +73,7 @@ __device__ void panel_minus_v_times(cplx<R>* A, int64_t lda, int M, int nc, cons
     }
     cplx<R>* a0p = A + (int64_t)c0 * lda;
     cplx<R>* a1p = a0p + lda;
+#pragma unroll 4
     for (int r = lane; r < M; r += 32) {
       cplx<R> s0 = mk<R>(0, 0), s1 = mk<R>(0, 0);
 #pragma unroll
