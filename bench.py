@@ -215,6 +215,17 @@ def per_update_error(st, r, prec):
 _T0 = time.perf_counter()
 
 
+def _jsonable(x):
+    """NumPy scalars and arrays in the JSON line."""
+    if isinstance(x, np.ndarray):
+        return x.tolist()
+    if isinstance(x, np.integer):
+        return int(x)
+    if isinstance(x, np.floating):
+        return float(x)
+    raise TypeError(f"not JSON serialisable: {type(x).__name__}")
+
+
 def progress(msg):
     """Phase timestamps on stderr (the JSON line alone goes to stdout)."""
     print(f"[bench {time.perf_counter() - _T0:7.1f} s] {msg}", file=sys.stderr, flush=True)
@@ -439,15 +450,18 @@ def run_crosstalk(args, torch, rank, world):
         d = st.discarded()[0]
         row = {"chi": chi, "kappa": kap, "prec": prec, "updates_per_s": n2q / t, "evolve_s": t,
                "purity": pur, "purity_s": tp, "trace": float(st.trace()[0]), "disc_chi": float(d[0]),
-               "disc_kappa": float(d[1]), "max_bond": max(bonds), "max_kraus": max(kraus),
+               "disc_kappa": float(d[1]), "max_bond": int(max(bonds)), "max_kraus": int(max(kraus)),
                "zz_19_20": float(st.zz(19, 20)[0])}
         for ch in chans.values():
             ch.free()
         st.free()
         return row
 
+    rows = []
     with ClockSampler(dev.index) as clk:
-        rows = [one(chi, kap, args.prec) for chi, kap in settings]
+        for chi, kap in settings:
+            rows.append(one(chi, kap, args.prec))
+            progress("crosstalk setting done: " + json.dumps(rows[-1], default=_jsonable))
     ref = max(rows, key=lambda r: (r["chi"], r["kappa"]))
     for r in rows:
         r["purity_minus_largest"] = r["purity"] - ref["purity"]
@@ -459,6 +473,49 @@ def run_crosstalk(args, torch, rank, world):
         twin["purity_err_vs_fp64"] = base["purity"] - twin["purity"]
         twin["disc_err_vs_fp64"] = [base["disc_chi"] - twin["disc_chi"], base["disc_kappa"] - twin["disc_kappa"]]
     return {"rows": rows, "fp64": twin, "n2q": n2q, "ref": ref, "clocks": clk.summary()}
+
+
+def run_surrogate(args, torch, rank, world):
+    """The screening surrogate (MLP 16-256-256-256-2, BF16 operands, FP32 accumulation): per step one
+    screening pass over 65536 candidate parameter sets and one AdamW training step on a batch of 4096
+    samples (features and targets synthetic, of the model's input and output shapes)."""
+    from paper_2508_07610_gb300 import build as Bld
+    from paper_2508_07610_gb300 import surrogate as S
+
+    Bld.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    n_cand, n_train = 65536, 4096
+    model = S.Surrogate(torch, max_batch=n_cand, seed=7 + rank)
+    g = torch.Generator(device="cuda").manual_seed(11 + rank)
+    X = torch.rand(n_cand, model.in_dim, device="cuda", generator=g)
+    Xt = X[:n_train].contiguous()
+    Tt = torch.rand(n_train, model.out_dim, device="cuda", generator=g)
+    for _ in range(args.warmup):
+        model.forward(X)
+        model.gradients(Xt, Tt)
+        model.adamw(1e-3)
+    torch.cuda.synchronize()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    with ClockSampler(dev.index) as clk:
+        e0.record()
+        for _ in range(args.steps):
+            model.forward(X)
+        e1.record()
+        for _ in range(args.steps):
+            model.gradients(Xt, Tt)
+            model.adamw(1e-3)
+        e2.record()
+        torch.cuda.synchronize()
+    ms_screen = e0.elapsed_time(e1) / args.steps
+    ms_train = e1.elapsed_time(e2) / args.steps
+    d = model.dims
+    macs = sum(d[i] * d[i + 1] for i in range(len(d) - 1))
+    fl_fwd = 2.0 * macs * n_cand
+    fl_train = 3 * 2.0 * macs * n_train
+    return {"screen_per_s": n_cand / (ms_screen / 1e3), "train_samples_per_s": n_train / (ms_train / 1e3),
+            "ms_screen": ms_screen, "ms_train": ms_train, "tflops_fwd": fl_fwd / (ms_screen / 1e3) / 1e12,
+            "tflops_train": fl_train / (ms_train / 1e3) / 1e12, "params": model.n_params, "clocks": clk.summary()}
 
 
 def barrier(torch, world):
@@ -526,7 +583,7 @@ def main():
     ap.add_argument("--cpu-updates", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--prec", default="fp32", choices=["mixed", "fp32", "fp64"])
-    ap.add_argument("--workload", default="hea", choices=["hea", "qaoa", "crosstalk"])
+    ap.add_argument("--workload", default="hea", choices=["hea", "qaoa", "crosstalk", "surrogate"])
     ap.add_argument("--settings", default="32,4;32,8;32,16;64,4;64,8;64,16;128,4;128,8;128,16",
                     help="crosstalk sweep (chi,kappa) settings")
     ap.add_argument("--tc", action="store_true", help="qualifying complex64 products on the tcgen05 tensor cores")
@@ -557,7 +614,7 @@ def main():
                 "cpu_baseline": {"value": v, "unit": "updates/s", "cores": host_cores(), "kind": "oracle",
                                  "sample": "one 2q update per step on a random right-canonical n=20 chain"},
                 "e2e": {"value": v, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-        print(json.dumps(line))
+        print(json.dumps(line, default=_jsonable))
         return
 
     import torch
@@ -565,6 +622,25 @@ def main():
     if world > 1:
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         torch.distributed.init_process_group("nccl")
+    if args.workload == "surrogate":
+        if rank == 0:
+            res = run_surrogate(args, torch, rank, world)
+            pk, src = peaks()
+            fp32_peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            line = {"metric": "surrogate screening candidates/s (MLP 16-256-256-256-2, 65536 per pass)",
+                    "value": res["screen_per_s"], "unit": "candidates/s", "n_gpus": 1, "steps": args.steps,
+                    "warmup": args.warmup, "ms_per_step": res["ms_screen"], "higher_is_better": True,
+                    "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+                    "config": {"workload": "screening pass over 65536 candidates; AdamW step on 4096 samples",
+                               "params": res["params"], "train_samples_per_s": res["train_samples_per_s"],
+                               "ms_train_step": res["ms_train"]},
+                    "roofline": {"kernel": "gemm_f32acc (forward)", "bound": "alu", "achieved": res["tflops_fwd"],
+                                 "peak": fp32_peak, "unit": "TFLOP/s", "frac": res["tflops_fwd"] / fp32_peak,
+                                 "traffic": None, "train_tflops": res["tflops_train"],
+                                 "peak_source": "FP32 FMA pipe from unit counts (BF16 operands, FP32 FMA)"},
+                    "clocks": res["clocks"]}
+            print(json.dumps(line, default=_jsonable))
+        return
     if args.workload == "crosstalk":
         if rank == 0:
             res = run_crosstalk(args, torch, rank, world)
@@ -578,7 +654,7 @@ def main():
                                "n2q": res["n2q"], "precision": args.prec, "settings": res["rows"],
                                "fp64_twin_of_smallest": res["fp64"]},
                     "clocks": res["clocks"]}
-            print(json.dumps(line))
+            print(json.dumps(line, default=_jsonable))
         return
     if args.workload == "qaoa":
         res = run_qaoa(args, torch, rank, world)
@@ -593,7 +669,7 @@ def main():
                                "n2q_per_pass": res["n2q_per_pass"], "mean_maxcut": res["maxcut_mean"],
                                "precision": args.prec},
                     "clocks": res["clocks"]}
-            print(json.dumps(line))
+            print(json.dumps(line, default=_jsonable))
         if world > 1:
             torch.distributed.destroy_process_group()
         return
@@ -656,7 +732,7 @@ def main():
             "e2e": {"value": res["e2e"], "unit": "updates/s", "h2d_bytes_per_step": res["h2d"],
                     "d2h_bytes_per_step": res["d2h"]},
             "gpu_launches": res["launches"], "roofline": roofline, "cpu_baseline": cpu}
-    print(json.dumps(line))
+    print(json.dumps(line, default=_jsonable))
     if world > 1:
         torch.distributed.destroy_process_group()
 
