@@ -31,6 +31,10 @@ sys.path.insert(0, ROOT)
 
 N_QUBITS, CHI, KAPPA = 20, 64, 8
 METRIC = "2q gate+channel+truncate updates/s at chi=64, kappa=8 (err<=1e-6 vs FP64); batched vs plain"
+# DRAM bytes (read + write) per launch of the single-shape call sites, from an ncu capture of the
+# steady-state workload with 128 chains per handle; valid for the kernels as captured and for 128
+# chains per group
+NCU_TRAFFIC_128 = {}
 
 
 def peaks():
@@ -694,7 +698,8 @@ def main():
     peak = 1.25 if (fp64_eig or args.prec == "fp64") else fp32_peak
     achieved = (fl_d / (ms_d / 1e3)) / 1e12 if ms_d > 0 else 0.0
     roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak,
+                "traffic": NCU_TRAFFIC_128.get(dom) if res["B"] // res["G"] == 128 else None,
                 "ms_per_step_in_kernel": ms_d, "launches_per_step": cnt_d,
                 "measured_on": f"group 0 alone ({res['B'] // res['G']} chains), two uncaptured layers, CUDA events "
                                "around every launch",

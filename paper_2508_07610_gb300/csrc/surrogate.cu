@@ -22,22 +22,24 @@ __device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float
 template <typename TA, typename TB>
 __global__ void __launch_bounds__(NT) gemm_f32acc(int M, int N, int K, const TA* A, int64_t as0, int64_t as1,
                                                   const TB* B, int64_t bs0, int64_t bs1, float* C, int64_t ldc,
-                                                  int accumulate) {
+                                                  int accumulate, int kc, float* ws) {
   __shared__ float As[TK][TM + 1];
   __shared__ float Bs[TK][TN + 1];
   const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  // K chunk of this CTA (split-K: blockIdx.z chunks of kc, partial tiles to ws)
+  const int kb = blockIdx.z * kc, ke = (K - kb < kc) ? K : kb + kc;
   float acc[4][4] = {};
-  for (int k0 = 0; k0 < K; k0 += TK) {
+  for (int k0 = kb; k0 < ke; k0 += TK) {
     for (int e = threadIdx.x; e < TM * TK; e += NT) {
       int i = e / TK, kk = e % TK;
       int gi = m0 + i, gk = k0 + kk;
-      As[kk][i] = (gi < M && gk < K) ? to_f(A[gi * as0 + gk * as1]) : 0.f;
+      As[kk][i] = (gi < M && gk < ke) ? to_f(A[gi * as0 + gk * as1]) : 0.f;
     }
     for (int e = threadIdx.x; e < TN * TK; e += NT) {
       int j = e % TN, kk = e / TN;
       int gj = n0 + j, gk = k0 + kk;
-      Bs[kk][j] = (gj < N && gk < K) ? to_f(B[gk * bs0 + gj * bs1]) : 0.f;
+      Bs[kk][j] = (gj < N && gk < ke) ? to_f(B[gk * bs0 + gj * bs1]) : 0.f;
     }
     __syncthreads();
 #pragma unroll
@@ -57,6 +59,10 @@ __global__ void __launch_bounds__(NT) gemm_f32acc(int M, int N, int K, const TA*
       int j = n0 + tx + 16 * c;
       if (j >= N) continue;
       float v = acc[r][c];
+      if (ws) {
+        ws[((int64_t)blockIdx.z * M + i) * N + j] = v;
+        continue;
+      }
       if (accumulate) v += C[(int64_t)i * ldc + j];
       C[(int64_t)i * ldc + j] = v;
     }
@@ -150,12 +156,42 @@ inline int grid_for(int64_t n) {
   return (int)(b < 1 ? 1 : (b > 4096 ? 4096 : b));
 }
 
+// C (+)= the sum of the sk partial tiles, added in a fixed order (deterministic)
+__global__ void splitk_sum(int M, int N, int sk, const float* ws, float* C, int64_t ldc, int accumulate) {
+  const int64_t MN = (int64_t)M * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < MN; e += (int64_t)gridDim.x * blockDim.x) {
+    float v = 0.f;
+    for (int t = 0; t < sk; ++t) v += ws[t * MN + e];
+    const int64_t o = (e / N) * ldc + e % N;
+    C[o] = accumulate ? C[o] + v : v;
+  }
+}
+
+// ws (nullable, ws_elems floats): workspace for split-K, used when the output has too few tiles for
+// the GPU and K is long (the weight gradients: 256 x 256 over the batch)
 template <typename TA, typename TB>
 cudaError_t gemm(cudaStream_t s, int M, int N, int K, const TA* A, int64_t as0, int64_t as1, const TB* B, int64_t bs0,
-                 int64_t bs1, float* C, int64_t ldc, int accumulate) {
+                 int64_t bs1, float* C, int64_t ldc, int accumulate, float* ws = nullptr, int64_t ws_elems = 0) {
   if (M <= 0 || N <= 0) return cudaSuccess;
-  dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM);
-  gemm_f32acc<TA, TB><<<grid, NT, 0, s>>>(M, N, K, A, as0, as1, B, bs0, bs1, C, ldc, accumulate);
+  const int tiles = ((N + TN - 1) / TN) * ((M + TM - 1) / TM);
+  int sk = 1;
+  if (ws && K >= 1024 && tiles < 304) {
+    sk = (304 + tiles - 1) / tiles;
+    if (sk > K / 256) sk = K / 256;
+    if (sk > 16) sk = 16;
+    while (sk > 1 && (int64_t)sk * M * N > ws_elems) --sk;
+    if (sk < 1) sk = 1;
+  }
+  const int kc = (sk > 1) ? ((K + sk - 1) / sk + TK - 1) / TK * TK : (K > 0 ? K : 1);
+  if (sk > 1) sk = (K + kc - 1) / kc;
+  dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, sk);
+  gemm_f32acc<TA, TB><<<grid, NT, 0, s>>>(M, N, K, A, as0, as1, B, bs0, bs1, C, ldc, accumulate, kc,
+                                          sk > 1 ? ws : nullptr);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || sk == 1) return e;
+  const int64_t mn = (int64_t)M * N;
+  splitk_sum<<<(unsigned)((mn + NT - 1) / NT < 1024 ? (mn + NT - 1) / NT : 1024), NT, 0, s>>>(M, N, sk, ws, C, ldc,
+                                                                                               accumulate);
   return cudaGetLastError();
 }
 }  // namespace
@@ -172,10 +208,12 @@ struct surr_ctx {
   std::vector<float*> Z;                                         // pre-activations per layer (FP32)
   std::vector<__nv_bfloat16*> H;                                 // activations per layer (BF16)
   float *d0 = nullptr, *d1 = nullptr;                            // gradient ping-pong buffers
+  float* ws = nullptr;                                           // split-K partials of the weight gradients
+  int64_t ws_elems = 0;
   double* dloss = nullptr;
   long long step = 0;
   ~surr_ctx() {
-    void* ptrs[] = {p, g, m, v, pb, xb, d0, d1, dloss};
+    void* ptrs[] = {p, g, m, v, pb, xb, d0, d1, ws, dloss};
     for (void* q : ptrs)
       if (q) cudaFree(q);
     for (auto* q : Z) cudaFree(q);
@@ -253,6 +291,12 @@ surr_status surr_create(int in_dim, int hidden, int n_hidden, int out_dim, int m
             cudaMalloc(&c->d0, sizeof(float) * (size_t)max_batch * std::max(hidden, out_dim)) == cudaSuccess &&
             cudaMalloc(&c->d1, sizeof(float) * (size_t)max_batch * std::max(hidden, out_dim)) == cudaSuccess &&
             cudaMalloc(&c->dloss, sizeof(double)) == cudaSuccess;
+  {
+    int64_t wmax = 0;
+    for (int l = 0; l < c->layers; ++l) wmax = std::max<int64_t>(wmax, (int64_t)c->dims[l] * c->dims[l + 1]);
+    c->ws_elems = 16 * wmax;
+    ok = ok && cudaMalloc(&c->ws, sizeof(float) * c->ws_elems) == cudaSuccess;
+  }
   for (int l = 0; ok && l < c->layers; ++l) {
     float* z = nullptr;
     __nv_bfloat16* a = nullptr;
@@ -333,7 +377,7 @@ surr_status surr_gradients(surr_t c, const float* X_dev, const float* T_dev, int
     const __nv_bfloat16* X = (l == 0) ? c->xb : c->H[l - 1];
     // dW = dZ^T X  (O x I), db = column sums of dZ
     if (gemm(s, O, I, batch, dcur, (int64_t)1, (int64_t)O, X, (int64_t)I, (int64_t)1, c->g + c->woff[l], (int64_t)I,
-             0) != cudaSuccess)
+             0, c->ws, c->ws_elems) != cudaSuccess)
       return SURR_ECUDA;
     bias_grad<<<O, 256, 0, s>>>(batch, O, dcur, c->g + c->boff[l]);
     if (cudaGetLastError() != cudaSuccess) return SURR_ECUDA;
