@@ -5,7 +5,9 @@
  *
  * Model: in_dim -> hidden (x n_hidden, GELU(z) = z (1 + erf(z / sqrt 2)) / 2) -> out_dim (linear).
  * Parameters are held as FP32 masters with a BF16 copy; forward and backward products take BF16
- * weights and activations and accumulate in FP32.  Loss: mean squared error over batch x out_dim.
+ * weights and activations and accumulate in FP32 (the forward products of layers 32..256 wide on the
+ * tensor cores, tcgen05 BF16 -> FP32; the rest on CUDA cores).  Loss: mean squared error over
+ * batch x out_dim.
  * Optimiser: AdamW with decoupled weight decay on the weight matrices only (not on the biases).
  * Parameter vector order: for each layer l, W_l (out x in, row-major) then b_l.
  * All *_dev pointers are device FP32 arrays, row-major batch x dim; work is enqueued on the
@@ -38,6 +40,8 @@ surr_status surr_adamw(surr_t s, float lr, float beta1, float beta2, float eps, 
 /* surr_gradients + surr_adamw(lr, 0.9, 0.999, 1e-8, weight_decay). */
 surr_status surr_train_step(surr_t s, const float* X_dev, const float* T_dev, int batch, float lr,
                             float weight_decay, double* loss_host);
+/* Wait for the handle's stream.  SURR_ECUDA also when a tensor-core launch gave up waiting for its
+ * matrix-multiply units (bounded wait; its output was left unwritten). */
 surr_status surr_sync(surr_t s);
 
 #ifdef __cplusplus

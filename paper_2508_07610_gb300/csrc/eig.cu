@@ -75,7 +75,7 @@ __device__ int sturm_count(const R* d, const R* e2, int n, R sigma, R pivmin) {
 }
 
 template <typename R, int NB>
-__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) heevk_kernel(EigArgs<R> g, int use_low) {
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) heevk_kernel(EigArgs<R> g) {
   __shared__ R red[NT / 32];
   __shared__ R s_d[MAXN], s_e2[MAXN], s_beta[MAXN];
   __shared__ cplx<R> s_p[MAXN], s_v[MAXN];
@@ -106,10 +106,6 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) heevk_kernel(EigAr
   cplx<R>* Vb = reinterpret_cast<cplx<R>*>(eig_dyn);  // NB x n, reflector l at Vb + l * n
   cplx<R>* Wb = Vb + (size_t)NB * n;                  // NB x n
   __shared__ cplx<R> s_x[2 * NB];
-  // with use_low: per-warp partial products of the lower-triangle matrix-vector product (NT/32 x n),
-  // placed after the Gram-Schmidt block buffer; only the lower triangle of the trailing block is read
-  // and updated, halving the traffic of the reduction
-  cplx<R>* Pw = reinterpret_cast<cplx<R>*>(reinterpret_cast<R*>(Wb + (size_t)NB * n) + (size_t)GB * k);
   for (int j0 = 0; j0 + 2 < n; j0 += NB) {
     const int pb = (n - 2 - j0 < NB) ? n - 2 - j0 : NB;
     for (int jj = 0; jj < pb; ++jj) {
@@ -155,36 +151,6 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) heevk_kernel(EigAr
         }
         __syncthreads();
         // p = beta (A_sub v - V x1 - W x2) on rows j+1..
-        if (use_low) {
-          // column c (one warp) adds a_ic v_c to row i >= c and conj(a_ic) v_i to row c
-          cplx<R>* P = Pw + (size_t)wid * n;
-          for (int i = j + 1 + lane; i < n; i += 32) P[i] = mk<R>(0, 0);
-          __syncwarp();
-          for (int c = j + 1 + wid; c < n; c += NT / 32) {
-            const cplx<R> vc = s_v[c];
-            const cplx<R>* colc = A + (int64_t)c * n;
-            cplx<R> dot = mk<R>(0, 0);
-#pragma unroll 4
-            for (int i = c + lane; i < n; i += 32) {
-              const cplx<R> a = colc[i];
-              cfma(P[i], a, vc);
-              if (i > c) cfma_cj(dot, a, s_v[i]);
-            }
-            dot = panel::warp_csum(dot);
-            if (lane == 0) P[c] = P[c] + dot;
-            __syncwarp();
-          }
-          __syncthreads();
-          for (int i = j + 1 + tid; i < n; i += NT) {
-            cplx<R> acc = mk<R>(0, 0);
-            for (int w = 0; w < NT / 32; ++w) acc = acc + Pw[(size_t)w * n + i];
-            for (int l = 0; l < jj; ++l) {
-              acc = acc - Vb[l * n + i] * s_x[l];
-              acc = acc - Wb[l * n + i] * s_x[jj + l];
-            }
-            s_p[i] = beta * acc;
-          }
-        } else
         for (int i = j + 1 + tid; i < n; i += NT) {
           cplx<R> acc0 = mk<R>(0, 0), acc1 = mk<R>(0, 0), acc2 = mk<R>(0, 0), acc3 = mk<R>(0, 0);
           int c = j + 1;
@@ -223,7 +189,6 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) heevk_kernel(EigAr
     const int t0 = j0 + pb, nt = n - t0;
     for (int64_t e = tid; e < (int64_t)nt * nt; e += NT) {
       const int i = t0 + (int)(e % nt), c = t0 + (int)(e / nt);
-      if (use_low && i < c) continue;  // only the lower triangle is read
       cplx<R> v = A[(int64_t)c * n + i];
       for (int l = 0; l < pb; ++l) {
         v = v - Vb[l * n + i] * conjg(Wb[l * n + c]);
@@ -602,14 +567,13 @@ cudaError_t heevk(cudaStream_t s, int batch, const EigArgs<R>& g) {
   if (g.n > MAXN || g.k > g.n || g.k + 1 > MAXN / 2) return cudaErrorInvalidValue;
   constexpr int NB = 8;  // reflectors per panel (tridiagonalisation and back-transformation)
   const size_t bytes = 2 * sizeof(cplx<R>) * (size_t)NB * g.n + sizeof(R) * (size_t)GB * g.k;
-  const size_t bytes_low = bytes + sizeof(cplx<R>) * (size_t)(NT / 32) * g.n;
   static bool attr_set = false;
   static size_t dyn_max = 0;
   if (!attr_set) {
     cudaFuncAttributes fa;
     cudaError_t e = cudaFuncGetAttributes(&fa, heevk_kernel<R, NB>);
     if (e != cudaSuccess) return e;
-    const size_t want = 2 * sizeof(cplx<R>) * NB * MAXN + sizeof(R) * GB * (MAXN / 2) + sizeof(cplx<R>) * (NT / 32) * MAXN;
+    const size_t want = 2 * sizeof(cplx<R>) * NB * MAXN + sizeof(R) * GB * (MAXN / 2);
     const size_t cap = 227 * 1024 - fa.sharedSizeBytes;
     dyn_max = want < cap ? want : cap;
     e = cudaFuncSetAttribute(heevk_kernel<R, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
@@ -617,10 +581,7 @@ cudaError_t heevk(cudaStream_t s, int batch, const EigArgs<R>& g) {
     attr_set = true;
   }
   if (bytes > dyn_max) return cudaErrorInvalidValue;
-  // the lower-triangle product when its partial buffers fit (and, for FP32, two CTAs still share an SM)
-  const size_t two_per_sm = 110 * 1024;
-  const bool low = bytes_low <= dyn_max && (sizeof(R) == 8 || bytes_low <= two_per_sm);
-  heevk_kernel<R, NB><<<batch, NT, low ? bytes_low : bytes, s>>>(g, low ? 1 : 0);
+  heevk_kernel<R, NB><<<batch, NT, bytes, s>>>(g);
   return cudaGetLastError();
 }
 

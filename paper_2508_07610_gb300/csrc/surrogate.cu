@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "surrogate.h"
+#include "surrogate_tc.h"
 
 namespace {
 constexpr int TM = 64, TN = 64, TK = 16, NT = 256;
@@ -237,10 +238,14 @@ surr_status forward(surr_ctx* c, const float* X, int Bn) {
   for (int l = 0; l < c->layers; ++l) {
     int I = c->dims[l], O = c->dims[l + 1];
     const __nv_bfloat16* W = c->pb + c->woff[l];
-    // Z = act W^T  (act: Bn x I, W: O x I)
-    if (gemm(s, Bn, O, I, act, (int64_t)I, (int64_t)1, W, (int64_t)1, (int64_t)I, c->Z[l], (int64_t)O, 0) !=
-        cudaSuccess)
+    // Z = act W^T  (act: Bn x I, W: O x I): on the tensor cores where the shape allows (the hidden
+    // layers), else on CUDA cores (the 2-wide output layer)
+    if (surr_tc::applicable(O, I, act, W)) {
+      if (surr_tc::linear(s, Bn, O, I, act, W, c->Z[l]) != cudaSuccess) return SURR_ECUDA;
+    } else if (gemm(s, Bn, O, I, act, (int64_t)I, (int64_t)1, W, (int64_t)1, (int64_t)I, c->Z[l], (int64_t)O, 0) !=
+               cudaSuccess) {
       return SURR_ECUDA;
+    }
     int last = (l == c->layers - 1);
     bias_act<<<grid_for((int64_t)Bn * O), NT, 0, s>>>(Bn, O, c->Z[l], c->p + c->boff[l], c->H[l], last ? 0 : 1);
     if (cudaGetLastError() != cudaSuccess) return SURR_ECUDA;
@@ -435,7 +440,10 @@ surr_status surr_train_step(surr_t c, const float* X_dev, const float* T_dev, in
 
 surr_status surr_sync(surr_t c) {
   if (!c) return SURR_EINVAL;
-  return cudaStreamSynchronize(c->stream) == cudaSuccess ? SURR_OK : SURR_ECUDA;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SURR_ECUDA;
+  int fail = 0;
+  if (surr_tc::read_fail_flag(&fail) != cudaSuccess || fail) return SURR_ECUDA;
+  return SURR_OK;
 }
 
 }  // extern "C"

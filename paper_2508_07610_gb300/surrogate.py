@@ -79,6 +79,10 @@ class Surrogate:
         except Exception:
             pass
 
+    def sync(self):
+        """Wait for the handle's stream; raises if a tensor-core launch gave up waiting."""
+        _check(_lib().surr_sync(self.h), "surr_sync")
+
     def params(self) -> np.ndarray:
         out = np.zeros(self.n_params, dtype=np.float32)
         _check(_lib().surr_get_params(self.h, out.ctypes.data_as(C.POINTER(C.c_float))), "surr_get_params")

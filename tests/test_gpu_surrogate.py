@@ -46,6 +46,39 @@ def test_forward_gradients_and_adamw_match_fp64(torch):
     assert np.max(np.abs(model.params() - p_ref)) < 1e-6
 
 
+def _bf16(x):
+    """Round to the nearest BF16 (ties to even), returned as float64."""
+    f = np.ascontiguousarray(x, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def test_forward_matches_bf16_rounded_reference(torch):
+    """The forward pass (hidden layers on the tensor cores) against an FP64 evaluation that rounds the
+    weights, the input and every hidden activation to BF16 as the kernels do: only the FP32 summation
+    order differs, so the outputs agree far more closely than with the unrounded FP64 model; a
+    layout or descriptor mistake in the tensor-core path would show as an O(1) difference."""
+    model = S.Surrogate(torch, max_batch=4096, seed=9)
+    dims = model.dims
+    p = model.params().astype(np.float64)
+    rng = np.random.default_rng(4)
+    X = rng.normal(size=(1000, 16)).astype(np.float32)  # 1000 rows: a ragged last 128-row tile
+    layers, _ = OM.layout(dims)
+    a = _bf16(X)
+    for li, (w, b, i, o) in enumerate(layers):
+        W = _bf16(p[w:w + i * o].reshape(o, i))
+        z = a @ W.T + p[b:b + o]
+        if li + 1 < len(layers):
+            a = _bf16(OM.gelu(z))
+        else:
+            a = z
+    y = model.forward(torch.tensor(X, device="cuda")).cpu().numpy()
+    rel = np.linalg.norm(y - a) / np.linalg.norm(a)
+    assert rel < 2e-3, rel
+    assert model.sync() is None
+
+
 def test_training_fits_a_smooth_function(torch):
     rng = np.random.default_rng(1)
     X = rng.uniform(-1, 1, size=(8192, 16)).astype(np.float32)
