@@ -152,13 +152,22 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) heevk_kernel(EigAr
         __syncthreads();
         // p = beta (A_sub v - V x1 - W x2) on rows j+1..
         for (int i = j + 1 + tid; i < n; i += NT) {
+          // the column loads of a block of MV columns are all issued before any is used, so a
+          // thread has MV L2 requests in flight instead of one
+          constexpr int MV = 16;
           cplx<R> acc0 = mk<R>(0, 0), acc1 = mk<R>(0, 0), acc2 = mk<R>(0, 0), acc3 = mk<R>(0, 0);
           int c = j + 1;
-          for (; c + 3 < n; c += 4) {  // four independent loads in flight per step
-            cfma(acc0, A[(int64_t)c * n + i], s_v[c]);
-            cfma(acc1, A[(int64_t)(c + 1) * n + i], s_v[c + 1]);
-            cfma(acc2, A[(int64_t)(c + 2) * n + i], s_v[c + 2]);
-            cfma(acc3, A[(int64_t)(c + 3) * n + i], s_v[c + 3]);
+          for (; c + MV <= n; c += MV) {
+            cplx<R> a[MV];
+#pragma unroll
+            for (int u = 0; u < MV; ++u) a[u] = A[(int64_t)(c + u) * n + i];
+#pragma unroll
+            for (int u = 0; u < MV; u += 4) {
+              cfma(acc0, a[u], s_v[c + u]);
+              cfma(acc1, a[u + 1], s_v[c + u + 1]);
+              cfma(acc2, a[u + 2], s_v[c + u + 2]);
+              cfma(acc3, a[u + 3], s_v[c + u + 3]);
+            }
           }
           for (; c < n; ++c) cfma(acc0, A[(int64_t)c * n + i], s_v[c]);
           cplx<R> acc = (acc0 + acc1) + (acc2 + acc3);
@@ -187,14 +196,28 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) heevk_kernel(EigAr
     }
     // trailing block (rows and columns from t0 on): A -= V W^H + W V^H over the panel
     const int t0 = j0 + pb, nt = n - t0;
-    for (int64_t e = tid; e < (int64_t)nt * nt; e += NT) {
-      const int i = t0 + (int)(e % nt), c = t0 + (int)(e / nt);
-      cplx<R> v = A[(int64_t)c * n + i];
-      for (int l = 0; l < pb; ++l) {
-        v = v - Vb[l * n + i] * conjg(Wb[l * n + c]);
-        v = v - Wb[l * n + i] * conjg(Vb[l * n + c]);
+    // four elements per thread per pass, loaded together before any is updated
+    constexpr int EU = 4;
+    const int64_t nn = (int64_t)nt * nt;
+    for (int64_t e0 = tid; e0 < nn; e0 += (int64_t)NT * EU) {
+      cplx<R> v[EU];
+#pragma unroll
+      for (int u = 0; u < EU; ++u) {
+        const int64_t e = e0 + (int64_t)u * NT;
+        if (e < nn) v[u] = A[(int64_t)(t0 + (int)(e / nt)) * n + t0 + (int)(e % nt)];
       }
-      A[(int64_t)c * n + i] = v;
+#pragma unroll
+      for (int u = 0; u < EU; ++u) {
+        const int64_t e = e0 + (int64_t)u * NT;
+        if (e >= nn) continue;
+        const int i = t0 + (int)(e % nt), c = t0 + (int)(e / nt);
+        cplx<R> w = v[u];
+        for (int l = 0; l < pb; ++l) {
+          w = w - Vb[l * n + i] * conjg(Wb[l * n + c]);
+          w = w - Wb[l * n + i] * conjg(Vb[l * n + c]);
+        }
+        A[(int64_t)c * n + i] = w;
+      }
     }
     __syncthreads();
   }

@@ -73,19 +73,34 @@ __device__ void panel_minus_v_times(cplx<R>* A, int64_t lda, int M, int nc, cons
     }
     cplx<R>* a0p = A + (int64_t)c0 * lda;
     cplx<R>* a1p = a0p + lda;
-#pragma unroll 4
-    for (int r = lane; r < M; r += 32) {
-      cplx<R> s0 = mk<R>(0, 0), s1 = mk<R>(0, 0);
+    // RU rows per lane per pass: their loads are issued together before any update is stored
+    constexpr int RU = 4;
+    for (int r0 = lane; r0 < M; r0 += 32 * RU) {
+      cplx<R> x0[RU], x1[RU];
 #pragma unroll
-      for (int i = 0; i < NB; ++i) {
-        if (i < pb) {
-          const cplx<R> v = Vs[i * ldv + r];
-          cfma(s0, v, y0[i]);
-          cfma(s1, v, y1[i]);
+      for (int u = 0; u < RU; ++u) {
+        const int r = r0 + 32 * u;
+        if (r < M) {
+          x0[u] = a0p[r];
+          x1[u] = two ? a1p[r] : mk<R>(0, 0);
         }
       }
-      a0p[r] = a0p[r] - s0;
-      if (two) a1p[r] = a1p[r] - s1;
+#pragma unroll
+      for (int u = 0; u < RU; ++u) {
+        const int r = r0 + 32 * u;
+        if (r >= M) continue;
+        cplx<R> s0 = mk<R>(0, 0), s1 = mk<R>(0, 0);
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+          if (i < pb) {
+            const cplx<R> v = Vs[i * ldv + r];
+            cfma(s0, v, y0[i]);
+            cfma(s1, v, y1[i]);
+          }
+        }
+        a0p[r] = x0[u] - s0;
+        if (two) a1p[r] = x1[u] - s1;
+      }
     }
   }
 }
