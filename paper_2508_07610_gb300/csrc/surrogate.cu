@@ -240,22 +240,15 @@ surr_status forward(surr_ctx* c, const float* X, int Bn) {
     const __nv_bfloat16* W = c->pb + c->woff[l];
     // Z = act W^T  (act: Bn x I, W: O x I): on the tensor cores where the shape allows (the hidden
     // layers), else on CUDA cores (the 2-wide output layer)
-    const int last = (l == c->layers - 1);
     if (surr_tc::applicable(O, I, act, W)) {
-      // bias, GELU and the BF16 copy in the tensor-core kernel's epilogue (hidden layers)
-      if (surr_tc::linear(s, Bn, O, I, act, W, c->Z[l], c->p + c->boff[l], last ? nullptr : c->H[l]) != cudaSuccess)
-        return SURR_ECUDA;
-      if (last) {
-        bias_act<<<grid_for((int64_t)Bn * O), NT, 0, s>>>(Bn, O, c->Z[l], c->p + c->boff[l], c->H[l], 0);
-        if (cudaGetLastError() != cudaSuccess) return SURR_ECUDA;
-      }
-    } else {
-      if (gemm(s, Bn, O, I, act, (int64_t)I, (int64_t)1, W, (int64_t)1, (int64_t)I, c->Z[l], (int64_t)O, 0) !=
-          cudaSuccess)
-        return SURR_ECUDA;
-      bias_act<<<grid_for((int64_t)Bn * O), NT, 0, s>>>(Bn, O, c->Z[l], c->p + c->boff[l], c->H[l], last ? 0 : 1);
-      if (cudaGetLastError() != cudaSuccess) return SURR_ECUDA;
+      if (surr_tc::linear(s, Bn, O, I, act, W, c->Z[l]) != cudaSuccess) return SURR_ECUDA;
+    } else if (gemm(s, Bn, O, I, act, (int64_t)I, (int64_t)1, W, (int64_t)1, (int64_t)I, c->Z[l], (int64_t)O, 0) !=
+               cudaSuccess) {
+      return SURR_ECUDA;
     }
+    int last = (l == c->layers - 1);
+    bias_act<<<grid_for((int64_t)Bn * O), NT, 0, s>>>(Bn, O, c->Z[l], c->p + c->boff[l], c->H[l], last ? 0 : 1);
+    if (cudaGetLastError() != cudaSuccess) return SURR_ECUDA;
     act = c->H[l];
   }
   return SURR_OK;

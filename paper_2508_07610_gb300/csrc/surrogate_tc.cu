@@ -8,8 +8,6 @@
 // K is staged in chunks of up to 64 through two shared-memory stages; one thread issues the K/16
 // MMAs of a chunk and commits them to the stage's mbarrier.  Every mbarrier wait is bounded: on
 // timeout the kernel raises a device flag (read by surr_sync) and leaves its output unwritten.
-// The epilogue adds the bias and, for a hidden layer, also writes GELU(Z) in BF16 (the next layer's
-// input), so the pre-activations are not read back by a separate pass.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -65,8 +63,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
 __device__ __forceinline__ int chunk_off(int row, int c8, int kc) { return (row >> 3) * (kc / 8) * 128 + c8 * 128 + (row & 7) * 16; }
 
 __global__ void __launch_bounds__(NTH) linear_kernel(int Bn, int O, int I, const __nv_bfloat16* act,
-                                                     const __nv_bfloat16* W, float* Z, int ncols, const float* bias,
-                                                     __nv_bfloat16* H) {
+                                                     const __nv_bfloat16* W, float* Z, int ncols) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int a_bytes = TM * KC * 2, b_bytes = ncols * KC * 2;
   const int stage_bytes = a_bytes + b_bytes;
@@ -161,13 +158,9 @@ __global__ void __launch_bounds__(NTH) linear_kernel(int Bn, int O, int I, const
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
     if (!ok || row >= Bn) continue;
     float* zr = Z + (int64_t)row * O;
-    __nv_bfloat16* hr = H ? H + (int64_t)row * O : nullptr;
     for (int c = 0; c < 16; ++c) {
       const int j = c0 + c;
-      if (j >= O) break;
-      const float z = __uint_as_float(r[c]) + (bias ? bias[j] : 0.f);
-      zr[j] = z;
-      if (hr) hr[j] = __float2bfloat16_rn(0.5f * z * (1.f + erff(z * 0.70710678118654752f)));  // GELU
+      if (j < O) zr[j] = __uint_as_float(r[c]);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -184,8 +177,7 @@ bool applicable(int O, int I, const void* act, const void* W) {
          (reinterpret_cast<uintptr_t>(W) & 15) == 0;
 }
 
-cudaError_t linear(cudaStream_t s, int Bn, int O, int I, const __nv_bfloat16* act, const __nv_bfloat16* W, float* Z,
-                   const float* bias, __nv_bfloat16* H) {
+cudaError_t linear(cudaStream_t s, int Bn, int O, int I, const __nv_bfloat16* act, const __nv_bfloat16* W, float* Z) {
   if (Bn <= 0) return cudaSuccess;
   if (!applicable(O, I, act, W)) return cudaErrorInvalidValue;
   int ncols = 32;  // TMEM columns: a power of two >= 32 that holds O
@@ -199,7 +191,7 @@ cudaError_t linear(cudaStream_t s, int Bn, int O, int I, const __nv_bfloat16* ac
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  linear_kernel<<<(Bn + TM - 1) / TM, NTH, bytes, s>>>(Bn, O, I, act, W, Z, ncols, bias, H);
+  linear_kernel<<<(Bn + TM - 1) / TM, NTH, bytes, s>>>(Bn, O, I, act, W, Z, ncols);
   return cudaGetLastError();
 }
 
