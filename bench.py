@@ -316,7 +316,7 @@ def run_ours(args, torch, rank, world):
     launches = per_step * args.steps
     ms_max = allreduce_max(torch, world, ms)
     total_2q = allreduce_sum(torch, world, n2q)
-    value = total_2q / (ms_max / 1e3)
+    value = replica_value(torch, world, n2q, ms)
     disc = st.discarded()
     # ---- per-kernel-class timing of the same layers on group 0 alone (CUDA events around every
     # launch, no graph, no other group running)
@@ -522,6 +522,12 @@ def run_surrogate(args, torch, rank, world):
             "tflops_train": fl_train / (ms_train / 1e3) / 1e12, "params": model.n_params, "clocks": clk.summary()}
 
 
+# Replicas only: every rank runs its own chains; the ranks meet only in these host-side reductions of
+# the timing (max over ranks) and of the work done (sum over ranks).
+def _reduce_device(torch):
+    return "cuda" if torch.distributed.get_backend() == "nccl" else "cpu"
+
+
 def barrier(torch, world):
     if world > 1:
         torch.distributed.barrier()
@@ -530,7 +536,7 @@ def barrier(torch, world):
 def allreduce_max(torch, world, x):
     if world == 1:
         return x
-    t = torch.tensor([float(x)], device="cuda")
+    t = torch.tensor([float(x)], device=_reduce_device(torch))
     torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
     return float(t.item())
 
@@ -538,9 +544,15 @@ def allreduce_max(torch, world, x):
 def allreduce_sum(torch, world, x):
     if world == 1:
         return x
-    t = torch.tensor([float(x)], device="cuda")
+    t = torch.tensor([float(x)], device=_reduce_device(torch))
     torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
     return float(t.item())
+
+
+def replica_value(torch, world, units, ms):
+    """Whole-job throughput of independent replicas: the units all ranks processed over the slowest
+    rank's time (ms)."""
+    return allreduce_sum(torch, world, units) / (allreduce_max(torch, world, ms) / 1e3)
 
 
 # ---------------------------------------------------------------------------------------- CPU reference
