@@ -7,13 +7,14 @@
 // (chi -> Kraus) uses it with k = n in FP64.
 //
 // Steps: (1) Householder reduction to a complex Hermitian tridiagonal (matrix kept in global
-// memory, which the L2 holds), followed by a diagonal phase change that makes it real symmetric;
-// (2) bisection with Sturm counts for the top k eigenvalues, one thread per eigenvalue;
-// (3) inverse iteration on the tridiagonal (LU with partial pivoting) from distinct
-// pseudo-random starts, one thread per vector; (4) classical Gram-Schmidt applied twice, in
-// descending eigenvalue order, which also separates vectors of (near-)degenerate eigenvalues;
-// (5) back-transformation through the phases and the Householder reflectors, one warp per vector.
-// Every loop is bounded; the input matrix is overwritten.
+// memory, which the L2 holds), blocked in panels of NB reflectors whose (v, w) pairs stay in shared
+// memory, followed by a diagonal phase change that makes it real symmetric; (2) bisection with Sturm
+// counts for the top k eigenvalues, one thread per eigenvalue; (3) inverse iteration on the
+// tridiagonal (LU with partial pivoting) from distinct pseudo-random starts, one thread per vector;
+// (4) classical Gram-Schmidt applied twice, in descending eigenvalue order and in blocks of GB
+// vectors, which also separates vectors of (near-)degenerate eigenvalues; (5) back-transformation of
+// all k vectors through the phases and the Householder reflectors, NB reflectors at a time as one
+// block reflector.  Every loop is bounded; the input matrix is overwritten.
 #include "kernels.h"
 #include "panel.cuh"
 
