@@ -62,7 +62,9 @@ enum {
   MPDO_EXPECT_PURITY = 5,    /* Tr rho^2, 1 value per chain */
   MPDO_EXPECT_DISCARDED = 6, /* 3 values per chain: cumulative discarded weight of bond and Kraus-leg
                                 truncations, and the smallest relative eigenvalue gap at a cut */
-  MPDO_EXPECT_DIMS = 7       /* 2n-1 values: bond dims (n-1) then Kraus dims (n) */
+  MPDO_EXPECT_DIMS = 7,      /* 2n-1 values: bond dims (n-1) then Kraus dims (n) */
+  MPDO_EXPECT_PROB = 8       /* args = n bits z_0 .. z_{n-1} (0 or 1): <z| rho |z>, the probability of
+                                measuring the bitstring (Sec. IV's output distributions), 1 value per chain */
 };
 /* Every expectation except TRACE and DISCARDED is divided by Tr rho (Tr rho^2 by (Tr rho)^2). */
 

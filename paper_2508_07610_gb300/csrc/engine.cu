@@ -839,6 +839,11 @@ struct Eng : EngBase {
 
   // <a| rho |b> element transfer for a, b in {0, 1} on every site
   mpdo_status element_(int a, int bsel, std::vector<double>& re, std::vector<double>& im) {
+    return element_bits(std::vector<int>(n, a), std::vector<int>(n, bsel), re, im);
+  }
+  // <a| rho |b> for computational-basis strings a, b (one physical index per site)
+  mpdo_status element_bits(const std::vector<int>& a, const std::vector<int>& bb, std::vector<double>& re,
+                           std::vector<double>& im) {
     C* Ea = wE;
     C* Eb = wT;
     mpdo_status st = one_env(Ea);
@@ -848,11 +853,11 @@ struct Eng : EngBase {
       const int N = dn * dr;
       const C* A = site_ptr(q);
       // tmp[l'][(n, r)] = sum_l E[l, l'] A[l, a, n, r]
-      st = gemm_(dl, N, dl, Ea, v2(sEnv, 0, 0, 1, 0, 0, dl), A + (int64_t)a * N, v2(slot_elems, 0, 0, 2 * N, 0, 0, 1),
+      st = gemm_(dl, N, dl, Ea, v2(sEnv, 0, 0, 1, 0, 0, dl), A + (int64_t)a[q] * N, v2(slot_elems, 0, 0, 2 * N, 0, 0, 1),
                  tmpA, row_major(N, sTmp));
       if (st) return st;
       // E'[r, r'] = sum_{(l', n)} tmp[(l', n), r] conj(A[l', b, n, r'])
-      st = gemm_(dr, dr, dl * dn, tmpA, v2(sTmp, 0, 0, 1, 0, 0, dr), A + (int64_t)bsel * N,
+      st = gemm_(dr, dr, dl * dn, tmpA, v2(sTmp, 0, 0, 1, 0, 0, dr), A + (int64_t)bb[q] * N,
                  v2(slot_elems, dn, (int64_t)2 * N, dr, 0, 0, 1, 1), Eb, row_major(dr, sEnv));
       if (st) return st;
       std::swap(Ea, Eb);
@@ -1046,6 +1051,19 @@ struct Eng : EngBase {
         return st;
       for (int b = 0; b < B; ++b) {
         out[b] = 0.5 * (r00[b] + r11[b] + 2 * r01[b]) / tr[b];
+        if (!finite(out[b])) return MPDO_ENOCONV;
+      }
+      return MPDO_OK;
+    }
+    if (kind == MPDO_EXPECT_PROB) {
+      if (nargs != n || !args) return MPDO_EINVAL;
+      std::vector<int> z(args, args + n);
+      for (int v : z)
+        if (v != 0 && v != 1) return MPDO_EINVAL;
+      std::vector<double> re, im;
+      if ((st = element_bits(z, z, re, im))) return st;
+      for (int b = 0; b < B; ++b) {
+        out[b] = re[b] / tr[b];
         if (!finite(out[b])) return MPDO_ENOCONV;
       }
       return MPDO_OK;

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libmpdo.so")
 
 FP64, MIXED, FP32 = 0, 1, 2
 PREC = {"fp64": FP64, "mixed": MIXED, "fp32": FP32}
-TRACE, ZZ, ZZ_MAP, GHZ, MAXCUT, PURITY, DISCARDED, DIMS = range(8)
+TRACE, ZZ, ZZ_MAP, GHZ, MAXCUT, PURITY, DISCARDED, DIMS, PROB = range(9)
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "not completely positive",
           4: "not trace preserving", 5: "non-finite result", 6: "timeout", 7: "CUDA error", 8: "invalid state"}
 
@@ -254,6 +254,21 @@ class MPDO:
     def maxcut(self, edges):
         return self._expect(MAXCUT, [x for e in edges for x in e])
 
+    def probability(self, bits):
+        """<z| rho |z> / Tr rho per chain for the bitstring z (bits[i] is qubit i's outcome)."""
+        return self._expect(PROB, tuple(int(v) for v in bits))
+
+    def probabilities(self) -> np.ndarray:
+        """The full output distribution per chain, batch x 2^n, basis index with qubit 0 most
+        significant (small n only: one readout sweep per bitstring)."""
+        if self.n > 16:
+            raise ValueError("probabilities(): n > 16")
+        out = np.zeros((self.batch, 1 << self.n))
+        for z in range(1 << self.n):
+            bits = [(z >> (self.n - 1 - i)) & 1 for i in range(self.n)]
+            out[:, z] = self.probability(bits)
+        return out
+
     def purity(self):
         return self._expect(PURITY)
 
@@ -325,3 +340,19 @@ def run_circuit(circuit, chi_max: int, kappa_max: int, prec="fp64", stream: int 
         (st.apply_1q if op.kind == 1 else st.apply_2q)(op.q, op.U, ch)
     st._channels = chans
     return st
+
+
+def jsd(p, q) -> float:
+    """Jensen-Shannon divergence (natural log) between two distributions over the same outcomes, the
+    distance the paper uses to compare output distributions: 0 for equal ones, ln 2 for disjoint ones."""
+    p = np.asarray(p, dtype=np.float64)
+    q = np.asarray(q, dtype=np.float64)
+    p = p / p.sum()
+    q = q / q.sum()
+    m = 0.5 * (p + q)
+
+    def kl(a):
+        nz = a > 0
+        return float(np.sum(a[nz] * np.log(a[nz] / m[nz])))
+
+    return 0.5 * kl(p) + 0.5 * kl(q)

@@ -165,6 +165,29 @@ def test_readouts_match_dense_definitions():
     assert abs(st.zz(3, 1)[0] - OD.expect_zz(rho, 5, 1, 3)) < 1e-11
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_bitstring_distribution_matches_oracle(prec):
+    """<z| rho |z> / Tr rho for all 32 bitstrings of a truncated n = 5 state against the diagonal of the
+    oracle's reconstructed rho (same truncations), and the Jensen-Shannon divergence between the two."""
+    circ = W.ghz_ansatz(n=5, depth=2)
+    st = G.run_circuit(circ, 8, 4, prec)
+    orc = OM.run_circuit(circ, 8, 4)
+    rho = orc.dense()
+    p_o = OD.probabilities(rho / np.trace(rho))
+    p_g = st.probabilities()[0]
+    tol_r, _, eps = TOL[prec]
+    lim = tol_r + 4 * orc.cut_sensitivity(eps)
+    assert np.max(np.abs(p_g - p_o)) < lim
+    assert abs(p_g.sum() - 1) < lim
+    assert G.jsd(p_g, p_o) < 10 * lim
+    # a single bitstring through the C ABI, and argument checks
+    assert abs(st.probability([0] * 5)[0] - p_o[0]) < lim
+    with pytest.raises(G.MPDOError):
+        st.probability([0, 1, 2, 0, 0])
+    with pytest.raises(G.MPDOError):
+        st.probability([0, 1])
+
+
 # ------------------------------------------------------------------ batches
 def test_batch_with_per_chain_gates_and_channels():
     torch = pytest.importorskip("torch")
