@@ -1,4 +1,7 @@
-// Batched complex Householder QR, one CTA per matrix (CUDA cores, FP32 or FP64 complex).
+// Batched complex Householder QR (CUDA cores, FP32 or FP64 complex) in three variants chosen per
+// launch: a blocked one-CTA-per-matrix kernel (compact-WY panels in shared memory) for batches that
+// fill the GPU, a thread-block-cluster kernel that spreads one matrix over 2-8 CTAs for small batches,
+// and a plain one-CTA-per-matrix kernel when neither fits.
 //
 // Used to keep the chain in canonical form (QR sweeps, Sec. II.D / Fig. 3b) and to reduce the
 // left site of a two-site update to its (p, bond) block.  For an m x n input (read through a
