@@ -46,8 +46,11 @@ class MPDO:
         self.discarded_chi = 0.0
         self.discarded_kappa = 0.0
         self.min_gap = np.inf   # smallest (s_k^2 - s_{k+1}^2)/s_1^2 over truncations that cut
-        self.cuts = []          # (relative gap, s_k^2 / s_1^2) of every truncation that cuts
+        self.cuts = []          # (relative gap, kept count, s^2 of every truncation that cuts)
         self.log = []           # (kind, site, kept, available, discarded weight)
+        # optional (eps, rng): every matrix about to be SVD-truncated is perturbed by eps * max|entry|
+        # complex Gaussian noise first (models rounding; used only to pin cut_allowance)
+        self.perturb = None
 
     # ------------------------------------------------------------ canonical form
     def _shift_right(self, q: int) -> None:
@@ -83,16 +86,39 @@ class MPDO:
         k = max(1, min(cap, nz))
         dropped = float(np.sum(s[k:] ** 2)) / total
         if k < nz:
-            gap = float((s[k - 1] ** 2 - s[k] ** 2) / s[0] ** 2)
+            s2 = s ** 2
+            gap = float((s2[k - 1] - s2[k]) / s2[0])
             self.min_gap = min(self.min_gap, gap)
-            self.cuts.append((gap, float(s[k - 1] ** 2 / s[0] ** 2)))
+            self.cuts.append((gap, k, s2.copy()))
         return k, dropped
 
-    def cut_sensitivity(self, eps: float) -> float:
-        """First-order bound on how far a readout can move when every truncation's Gram matrix is
-        perturbed by eps (relative to its largest eigenvalue): a perturbation rotates the last kept
-        and first dropped directions by about min(1, eps / gap), which moves weight s_k^2 / s_1^2."""
-        return float(sum(min(1.0, eps / g) * w if g > 0 else w for g, w in self.cuts))
+    def _perturbed(self, M: np.ndarray) -> np.ndarray:
+        if self.perturb is None:
+            return M
+        eps, rng = self.perturb
+        noise = rng.normal(size=M.shape) + 1j * rng.normal(size=M.shape)
+        return M + (eps * np.max(np.abs(M)) / np.sqrt(2)) * noise
+
+    def cut_allowance(self, threshold: float) -> float:
+        """Allowance on a normalised readout (operator norm 1) for truncations that cut inside a
+        near-degenerate cluster, where the truncation of Sec. II.D is not unique.
+
+        A cut with relative gap (s_k^2 - s_{k+1}^2) / s_1^2 >= threshold contributes nothing.  Below
+        it, the kept directions whose s_i^2 lies within threshold * s_1^2 of the first dropped one
+        may be exchanged for dropped directions of the same cluster.  Exchanging directions of total
+        weight W (in units of the unnormalised state, since sum s^2 = Tr rho with the centre on the
+        truncated site) moves the state by at most 2 W in trace norm, and the normalisation by the
+        final trace T doubles that bound for Tr(rho O) / Tr rho.  The sum over such cuts of 4 W / T is
+        returned; it is 0 when every cut is separated by at least `threshold`."""
+        bad = [(k, s2) for gap, k, s2 in self.cuts if gap < threshold]
+        if not bad:
+            return 0.0
+        tf = self.trace()
+        a = 0.0
+        for k, s2 in bad:
+            near = (s2[:k] - s2[k]) < threshold * s2[0]
+            a += 4.0 * float(np.sum(s2[:k][near])) / tf
+        return a
 
     def truncate_kraus(self, q: int, kappa: int = 0) -> float:
         """Eq. (svdNoise): T as a (p, l, r) x n matrix = U S V^dag; keep the top kappa; T' = T V."""
@@ -100,7 +126,7 @@ class MPDO:
         self.move_centre(q)
         A = self.sites[q]
         dl, _, dn, dr = A.shape
-        M = A.transpose(0, 1, 3, 2).reshape(dl * 2 * dr, dn)
+        M = self._perturbed(A.transpose(0, 1, 3, 2).reshape(dl * 2 * dr, dn))
         _, s, Vh = np.linalg.svd(M, full_matrices=False)
         k, w = self._keep(s, cap)
         Mt = M @ Vh[:k].conj().T
@@ -136,7 +162,7 @@ class MPDO:
         K = np.stack([N @ U for N in kraus]).reshape(rk, 2, 2, 2, 2)  # [k, p1', p2', p1, p2]
         theta = np.einsum("lanb,bcmr->lancmr", A1, A2)                # [l, p1, n1, p2, n2, r]
         theta = np.einsum("kxyac,lancmr->lxnykmr", K, theta)          # [l, p1', n1, p2', k, n2, r]
-        mat = theta.reshape(dl * 2 * dn1, 2 * rk * dn2 * dr)
+        mat = self._perturbed(theta.reshape(dl * 2 * dn1, 2 * rk * dn2 * dr))
         Um, s, Vh = np.linalg.svd(mat, full_matrices=False)
         k, w = self._keep(s, self.chi_max)
         self.sites[q] = Um[:, :k].reshape(dl, 2, dn1, k)
@@ -222,10 +248,12 @@ class MPDO:
         return [A.shape[2] for A in self.sites]
 
 
-def run_circuit(circuit, chi_max: int, kappa_max: int, tol: float = 1e-13, kraus_tol: float = 1e-12) -> MPDO:
+def run_circuit(circuit, chi_max: int, kappa_max: int, tol: float = 1e-13, kraus_tol: float = 1e-12,
+                perturb=None) -> MPDO:
     """Convert every channel from its chi matrix (Sec. III) and apply the ops in order."""
     kraus = [chi_to_kraus(chi, nq, kraus_tol) for nq, chi in circuit.chis]
     st = MPDO(circuit.n, chi_max, kappa_max, tol)
+    st.perturb = perturb
     for op in circuit.ops:
         if op.kind == 1:
             st.apply_1q(op.q, op.U, kraus[op.chan])

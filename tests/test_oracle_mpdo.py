@@ -139,3 +139,53 @@ def test_truncation_converges_with_caps():
         errs.append(abs(M.run_circuit(circ, chi, kap).ghz_fidelity() - f_exact))
     assert errs[-1] < 1e-12
     assert errs[0] > errs[-1]
+
+
+# ------------------------------------------------------------------ the parity allowance at degenerate cuts
+def _readouts(st):
+    return np.concatenate([st.zz_map().ravel(), [st.ghz_fidelity(), st.purity()]])
+
+
+def _perturbed_spread(circ, chi, kap, eps, seeds=6):
+    """Largest readout change over runs whose every truncated matrix is perturbed by eps (relative)."""
+    base = M.run_circuit(circ, chi, kap)
+    r0 = _readouts(base)
+    d = max(float(np.max(np.abs(_readouts(M.run_circuit(circ, chi, kap, perturb=(eps, np.random.default_rng(s))))
+                                - r0))) for s in range(seeds))
+    return base, d
+
+
+def _degenerate_cut_circuit():
+    """DEP2(p) on |00>: the Kraus-leg Gram has eigenvalues (1 - 3p/4, p/4, p/4, p/4) (Sec. II.A's Kraus
+    set), so kappa = 2 cuts inside an exactly threefold cluster; later entangling gates make the choice
+    of the kept direction visible in the readouts."""
+    rng = np.random.default_rng(7)
+    chis = [(2, W.kraus_to_chi(W.depolarizing_2q(0.05))), (2, W.kraus_to_chi([np.eye(4)]))]
+    ops = [W.Op(2, 0, np.eye(4, dtype=np.complex128), 0)]
+    ops += [W.Op(2, q, W.random_unitary(4, rng), 1) for q in (1, 0, 1)]
+    return W.Circuit(3, ops, chis)
+
+
+def test_cut_allowance_bounds_a_degenerate_cut():
+    circ = _degenerate_cut_circuit()
+    for eps in (1e-13, 1e-7):  # FP64-like and complex64-like rounding
+        base, d = _perturbed_spread(circ, 8, 2, eps)
+        gaps = [g for g, _, _ in base.cuts]
+        assert min(gaps) < 1e-12                       # the cut is exactly degenerate
+        a = base.cut_allowance(1e-9)
+        assert a == base.cut_allowance(1e-5) > 0
+        assert d > 1e-3                                # the choice of subspace moves the readouts ...
+        assert d <= a                                  # ... by no more than the allowance
+        assert a < 10 * d                              # and the allowance is not vacuous (4 x p/4 / Tr rho)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_cut_allowance_is_zero_for_separated_cuts(seed):
+    rng = np.random.default_rng(1000 + seed)
+    circ = W.random_circuit(5, 20, rng, rank1=3, rank2=6)
+    base, d = _perturbed_spread(circ, 3, 2, 1e-13, seeds=3)
+    assert base.min_gap > 1e-3
+    assert base.cut_allowance(1e-5) == 0.0 and base.cut_allowance(1e-9) == 0.0
+    # rounding-level perturbations move the readouts only to first order in eps / gap
+    assert d < 1e-10
+    assert d < base.min_gap and d * base.min_gap / 1e-13 < 1.0
