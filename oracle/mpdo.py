@@ -16,7 +16,8 @@ Steps, in the paper's order:
     (p, l, r) x n matrix is SVD-truncated to kappa_max values, T' = U S (= T V).
 Readings where the paper is silent: truncation runs per gate with the
 orthogonality centre on the touched site (either site of a two-qubit gate); after a two-qubit gate the bond is
-split first and the right site's Kraus leg truncated second; nothing is
+split first and the right site's Kraus leg truncated second (trunc_order "split_first"; the order
+"kraus_first" truncates the merged tensor's new Kraus leg before the split); nothing is
 renormalised and every readout is divided by Tr(rho); singular values at or
 below tol * sigma_max are dropped as numerically zero.
 
@@ -33,7 +34,10 @@ from .channels import chi_to_kraus
 
 class MPDO:
     def __init__(self, n: int, chi_max: int, kappa_max: int, tol: float = 1e-13,
-                 auto_truncate: bool = True):
+                 auto_truncate: bool = True, trunc_order: str = "split_first"):
+        if trunc_order not in ("split_first", "kraus_first"):
+            raise ValueError(trunc_order)
+        self.trunc_order = trunc_order
         self.n = n
         self.chi_max = chi_max
         self.kappa_max = kappa_max
@@ -150,7 +154,8 @@ class MPDO:
     def apply_2q(self, q: int, U: np.ndarray, kraus) -> None:
         """Two-site update on (q, q+1): merge, apply K_k = N_k U with a new Kraus leg on site q+1,
         split by the SVD of the (l, p1, n1) x (p2, k, n2, r) matrix keeping chi_max values, then
-        truncate the Kraus leg of site q+1.  The split only needs every site left of q
+        truncate the Kraus leg of site q+1 ("split_first").  With trunc_order "kraus_first" the new
+        Kraus leg of the merged tensor is truncated first and the bond split second.  The split only needs every site left of q
         left-isometric and every site right of q+1 right-isometric, so the centre may sit on either
         of the two sites; it is moved only when it is elsewhere."""
         if self.centre not in (q, q + 1):
@@ -162,15 +167,27 @@ class MPDO:
         K = np.stack([N @ U for N in kraus]).reshape(rk, 2, 2, 2, 2)  # [k, p1', p2', p1, p2]
         theta = np.einsum("lanb,bcmr->lancmr", A1, A2)                # [l, p1, n1, p2, n2, r]
         theta = np.einsum("kxyac,lancmr->lxnykmr", K, theta)          # [l, p1', n1, p2', k, n2, r]
-        mat = self._perturbed(theta.reshape(dl * 2 * dn1, 2 * rk * dn2 * dr))
+        dk = rk * dn2
+        if self.auto_truncate and self.trunc_order == "kraus_first":
+            # Eq. (svdNoise) on the merged tensor first: its new Kraus leg (k, n2) against all other
+            # indices (l, p1', n1, p2', r), keep kappa_max values; the bond split below then sees the
+            # already truncated leg and site q+1 needs no second Kraus truncation
+            M = self._perturbed(theta.reshape(dl, 2, dn1, 2, dk, dr).transpose(0, 1, 2, 3, 5, 4).reshape(-1, dk))
+            _, sk, Vkh = np.linalg.svd(M, full_matrices=False)
+            nu, wk = self._keep(sk, self.kappa_max)
+            theta = (M @ Vkh[:nu].conj().T).reshape(dl, 2, dn1, 2, dr, nu).transpose(0, 1, 2, 3, 5, 4)
+            self.discarded_kappa += wk
+            self.log.append(("kappa", q + 1, nu, len(sk), wk))
+            dk = nu
+        mat = self._perturbed(theta.reshape(dl * 2 * dn1, 2 * dk * dr))
         Um, s, Vh = np.linalg.svd(mat, full_matrices=False)
         k, w = self._keep(s, self.chi_max)
         self.sites[q] = Um[:, :k].reshape(dl, 2, dn1, k)
-        self.sites[q + 1] = (s[:k, None] * Vh[:k]).reshape(k, 2, rk * dn2, dr)
+        self.sites[q + 1] = (s[:k, None] * Vh[:k]).reshape(k, 2, dk, dr)
         self.centre = q + 1
         self.discarded_chi += w
         self.log.append(("chi", q, k, len(s), w))
-        if self.auto_truncate:
+        if self.auto_truncate and self.trunc_order == "split_first":
             self.truncate_kraus(q + 1)
 
     # ------------------------------------------------------------ readouts
@@ -249,10 +266,10 @@ class MPDO:
 
 
 def run_circuit(circuit, chi_max: int, kappa_max: int, tol: float = 1e-13, kraus_tol: float = 1e-12,
-                perturb=None) -> MPDO:
+                perturb=None, trunc_order: str = "split_first") -> MPDO:
     """Convert every channel from its chi matrix (Sec. III) and apply the ops in order."""
     kraus = [chi_to_kraus(chi, nq, kraus_tol) for nq, chi in circuit.chis]
-    st = MPDO(circuit.n, chi_max, kappa_max, tol)
+    st = MPDO(circuit.n, chi_max, kappa_max, tol, trunc_order=trunc_order)
     st.perturb = perturb
     for op in circuit.ops:
         if op.kind == 1:

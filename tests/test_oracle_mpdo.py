@@ -189,3 +189,44 @@ def test_cut_allowance_is_zero_for_separated_cuts(seed):
     # rounding-level perturbations move the readouts only to first order in eps / gap
     assert d < 1e-10
     assert d < base.min_gap and d * base.min_gap / 1e-13 < 1.0
+
+
+# ------------------------------------------------------------------ truncation order (Sec. II.D schedules)
+@pytest.mark.parametrize("seed", range(3))
+def test_kraus_first_equals_split_first_when_the_bond_is_not_cut(seed):
+    """With chi_max at least every bond's rank the split is exact, and the Kraus leg of site q+1 after
+    the split has the same Gram (ancilla density) as the merged tensor's leg: both orders keep the
+    same subspace and give the same state."""
+    rng = np.random.default_rng(300 + seed)
+    circ = W.random_circuit(4, 14, rng, rank1=3, rank2=6)
+    a = M.run_circuit(circ, 4096, 3, trunc_order="split_first")
+    b = M.run_circuit(circ, 4096, 3, trunc_order="kraus_first")
+    assert a.discarded_chi < 1e-24 and b.discarded_chi < 1e-24
+    assert a.discarded_kappa > 1e-6
+    assert abs(a.discarded_kappa - b.discarded_kappa) < 1e-12
+    assert np.max(np.abs(a.dense() - b.dense())) < 1e-12
+
+
+def test_kraus_first_exact_when_caps_cover_ranks():
+    rng = np.random.default_rng(17)
+    circ = W.random_circuit(4, 12, rng, rank1=3, rank2=5)
+    st = M.run_circuit(circ, 64, 4096, trunc_order="kraus_first")
+    assert st.discarded_chi < 1e-24 and st.discarded_kappa < 1e-24
+    assert np.max(np.abs(st.dense() - D.run_circuit(circ))) < 1e-12
+
+
+def test_kraus_first_under_truncation_is_a_valid_state_close_to_split_first():
+    circ = W.ghz_ansatz(n=6, depth=3)
+    exact = D.run_circuit(circ)
+    a = M.run_circuit(circ, 6, 2)
+    b = M.run_circuit(circ, 6, 2, trunc_order="kraus_first")
+    rho = b.dense() / b.trace()
+    assert np.max(np.abs(rho - rho.conj().T)) < 1e-13
+    assert np.linalg.eigvalsh(rho).min() > -1e-13
+    assert b.discarded_chi > 0 and b.discarded_kappa > 0
+    # both schedules approximate the same exact state about equally well
+    ea = abs(a.ghz_fidelity() - D.ghz_fidelity(exact, 6))
+    eb = abs(b.ghz_fidelity() - D.ghz_fidelity(exact, 6))
+    assert eb < 10 * ea + 1e-3 and ea < 10 * eb + 1e-3
+    # every kappa cut of kraus_first happens inside the two-qubit update (no separate truncation of q+1)
+    assert sum(1 for e in b.log if e[0] == "kappa") == sum(1 for e in a.log if e[0] == "kappa")
