@@ -15,6 +15,14 @@
 // vectors, which also separates vectors of (near-)degenerate eigenvalues; (5) back-transformation of
 // all k vectors through the phases and the Householder reflectors, NB reflectors at a time as one
 // block reflector.  Every loop is bounded; the input matrix is overwritten.
+//
+// FP64 on this GPU has 1/64 of the FP32 issue rate, so the FP64 instantiation saves FP64 operations
+// where it can without losing accuracy: the reduction updates only the lower triangle of the
+// trailing block, the off-diagonal magnitudes are taken once, and the substitutions of the inverse
+// iteration multiply by reciprocal pivots instead of dividing.  (Shifts from an FP32 bisection were
+// tried and rejected: they cannot separate eigenvalues closer than about u32 ||T||, and cuts with
+// relative gaps between 1e-9 and 1e-6 then lost FP64 accuracy.)
+#include "device_once.cuh"
 #include "kernels.h"
 #include "panel.cuh"
 
@@ -60,6 +68,14 @@ __device__ __forceinline__ float eps_of<float>() { return 1.1920929e-07f; }
 template <>
 __device__ __forceinline__ double eps_of<double>() { return 2.220446049250313e-16; }
 
+// FP64 runs on a pipe 64 times narrower than FP32 on this GPU, so in FP64 the reduction keeps only the
+// lower triangle of the trailing block up to date (a third fewer FP64 operations); in FP32, where
+// the kernel is bound by latency rather than arithmetic, the full square is cheaper to address.
+template <typename R>
+__host__ __device__ constexpr bool kLowerOnly() {
+  return sizeof(R) == 8;
+}
+
 // number of eigenvalues of the real symmetric tridiagonal (d, e2 = e^2) below sigma
 template <typename R>
 __device__ int sturm_count(const R* d, const R* e2, int n, R sigma, R pivmin) {
@@ -78,14 +94,15 @@ __device__ int sturm_count(const R* d, const R* e2, int n, R sigma, R pivmin) {
 template <typename R, int NB>
 __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) heevk_kernel(EigArgs<R> g) {
   __shared__ R red[NT / 32];
-  __shared__ R s_d[MAXN], s_e2[MAXN], s_beta[MAXN];
+  __shared__ R s_d[MAXN], s_e2[MAXN], s_beta[MAXN], s_eabs[MAXN];
   __shared__ cplx<R> s_p[MAXN], s_v[MAXN];
   __shared__ R s_w[MAXN];
   __shared__ cplx<R> s_v0[MAXN];
-  __shared__ int s_flag;
+  __shared__ int s_flag, s_bad;
   const int z = blockIdx.x;
   const int n = g.n, k = g.k;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) s_bad = 0;
   cplx<R>* A = g.A + (int64_t)z * g.astride;
   R* S = g.scratch + (int64_t)z * g.sstride;
   // scratch layout (R units, vector t element i at [i * k + t] so threads walk it coalesced)
@@ -152,6 +169,45 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) heevk_kernel(EigAr
         }
         __syncthreads();
         // p = beta (A_sub v - V x1 - W x2) on rows j+1..
+        if constexpr (kLowerOnly<R>()) {
+          // only the lower triangle of the trailing block is current: rows i take sum_{c <= i}
+          // A(i, c) v_c from the columns (coalesced over i), then one warp per column i adds
+          // sum_{c > i} conj(A(c, i)) v_c, the stored column read downwards
+          for (int i = j + 1 + tid; i < n; i += NT) {
+            constexpr int MV = 8;
+            cplx<R> acc0 = mk<R>(0, 0), acc1 = mk<R>(0, 0);
+            int c = j + 1;
+            for (; c + MV <= i + 1; c += MV) {
+              cplx<R> a[MV];
+#pragma unroll
+              for (int u = 0; u < MV; ++u) a[u] = A[(int64_t)(c + u) * n + i];
+#pragma unroll
+              for (int u = 0; u < MV; u += 2) {
+                cfma(acc0, a[u], s_v[c + u]);
+                cfma(acc1, a[u + 1], s_v[c + u + 1]);
+              }
+            }
+            for (; c <= i; ++c) cfma(acc0, A[(int64_t)c * n + i], s_v[c]);
+            s_p[i] = acc0 + acc1;
+          }
+          __syncthreads();
+          for (int i = j + 1 + wid; i + 1 < n; i += NT / 32) {
+            const cplx<R>* coli = A + (int64_t)i * n;
+            cplx<R> dot = mk<R>(0, 0);
+            for (int c = i + 1 + lane; c < n; c += 32) cfma_cj(dot, coli[c], s_v[c]);
+            dot = panel::warp_csum(dot);
+            if (lane == 0) s_p[i] = s_p[i] + dot;
+          }
+          __syncthreads();
+          for (int i = j + 1 + tid; i < n; i += NT) {
+            cplx<R> acc = s_p[i];
+            for (int l = 0; l < jj; ++l) {
+              acc = acc - Vb[l * n + i] * s_x[l];
+              acc = acc - Wb[l * n + i] * s_x[jj + l];
+            }
+            s_p[i] = beta * acc;
+          }
+        } else
         for (int i = j + 1 + tid; i < n; i += NT) {
           // the column loads of a block of MV columns are all issued before any is used, so a
           // thread has MV L2 requests in flight instead of one
@@ -205,13 +261,15 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) heevk_kernel(EigAr
 #pragma unroll
       for (int u = 0; u < EU; ++u) {
         const int64_t e = e0 + (int64_t)u * NT;
-        if (e < nn) v[u] = A[(int64_t)(t0 + (int)(e / nt)) * n + t0 + (int)(e % nt)];
+        const bool need = e < nn && !(kLowerOnly<R>() && (int)(e % nt) < (int)(e / nt));
+        if (need) v[u] = A[(int64_t)(t0 + (int)(e / nt)) * n + t0 + (int)(e % nt)];
       }
 #pragma unroll
       for (int u = 0; u < EU; ++u) {
         const int64_t e = e0 + (int64_t)u * NT;
         if (e >= nn) continue;
         const int i = t0 + (int)(e % nt), c = t0 + (int)(e / nt);
+        if (kLowerOnly<R>() && i < c) continue;  // the upper triangle is never read again
         cplx<R> w = v[u];
         for (int l = 0; l < pb; ++l) {
           w = w - Vb[l * n + i] * conjg(Wb[l * n + c]);
@@ -256,6 +314,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) heevk_kernel(EigAr
   const R abstol = eps * tnorm + pivmin;
   gl -= R(2) * eps * tnorm * n + pivmin;
   gu += R(2) * eps * tnorm * n + pivmin;
+  for (int i = tid; i < n; i += NT) s_eabs[i] = (i + 1 < n) ? sqrt(s_e2[i]) : R(0);
   for (int t = tid; t < kk; t += NT) {
     const int target = n - 1 - t;  // ascending index of the t-th largest eigenvalue
     R lo = gl, hi = gu;
@@ -277,16 +336,16 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) heevk_kernel(EigAr
     // LU with partial pivoting of T - lam I: factors dd (diagonal of U), du, du2 (its two upper
     // diagonals), dl (multipliers) and the row interchanges, row by row; (d, u) is the current row
     R d = s_d[0] - lam;
-    R u = (n > 1) ? sqrt(s_e2[0]) : R(0);
+    R u = (n > 1) ? s_eabs[0] : R(0);
     for (int i = 0; i + 1 < n; ++i) {
-      const R l = sqrt(s_e2[i]);
+      const R l = s_eabs[i];
       const R dn = s_d[i + 1] - lam;
-      const R un = (i + 2 < n) ? sqrt(s_e2[i + 1]) : R(0);
+      const R un = (i + 2 < n) ? s_eabs[i + 1] : R(0);
       const int64_t o = (int64_t)i * k + t;
       if (fabs(d) >= fabs(l)) {
         if (fabs(d) < pert) d = (d < R(0)) ? -pert : pert;
         const R f = l / d;
-        Ldd[o] = d;
+        Ldd[o] = R(1) / d;  // reciprocal pivots: the substitutions multiply
         Ldu[o] = u;
         Ldu2[o] = 0;
         Ldl[o] = f;
@@ -295,7 +354,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) heevk_kernel(EigAr
         u = un;
       } else {
         const R f = d / l;
-        Ldd[o] = l;
+        Ldd[o] = R(1) / l;
         Ldu[o] = dn;
         Ldu2[o] = un;
         Ldl[o] = f;
@@ -305,7 +364,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) heevk_kernel(EigAr
       }
     }
     if (fabs(d) < pert) d = (d < R(0)) ? -pert : pert;
-    Ldd[(int64_t)(n - 1) * k + t] = d;
+    Ldd[(int64_t)(n - 1) * k + t] = R(1) / d;
     // start vector
     for (int i = 0; i < n; ++i) {
       uint32_t h = hash32((uint32_t)(t * 7919 + 1) * 2654435761u ^ (uint32_t)(i * 40503 + 17));
@@ -368,7 +427,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) heevk_kernel(EigAr
             R v = y[c];
             if (i + 1 < n) v -= du[c] * z1;
             if (i + 2 < n) v -= du2[c] * z2;
-            v /= dd[c];
+            v *= dd[c];
             if (!(fabs(v) < R(1e30))) v = (v > 0) ? R(1e30) : R(-1e30);
             y[c] = v;
             zmax = fmax(zmax, fabs(v));
@@ -485,7 +544,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) heevk_kernel(EigAr
           R v = Zr[(int64_t)i * k + t];
           if (i + 1 < n) v -= Ldu[(int64_t)i * k + t] * Zr[(int64_t)(i + 1) * k + t];
           if (i + 2 < n) v -= Ldu2[(int64_t)i * k + t] * Zr[(int64_t)(i + 2) * k + t];
-          v /= Ldd[(int64_t)i * k + t];
+          v *= Ldd[(int64_t)i * k + t];
           if (!(fabs(v) < R(1e30))) v = (v > 0) ? R(1e30) : R(-1e30);
           Zr[(int64_t)i * k + t] = v;
           zmax = fmax(zmax, fabs(v));
@@ -565,9 +624,17 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) heevk_kernel(EigAr
     R* w = g.w + (int64_t)z * g.wstride;
     for (int t = tid; t < k; t += NT) w[t] = s_w[t];
   }
+  // non-finite eigenvalues, trace or eigenvector entries (from non-finite input: the inverse
+  // iteration's growth guard keeps finite inputs finite) are reported as non-convergence
+  for (int64_t e = tid; e < (int64_t)n * k; e += NT) {
+    const cplx<R> v = U[e];
+    if (!isfinite((double)v.x) || !isfinite((double)v.y)) s_bad = 1;
+  }
+  __syncthreads();
   if (tid == 0) {
     double kept = 0;
     for (int t = 0; t < k; ++t) kept += (double)s_w[t];
+    if (g.status && (s_bad || !isfinite(kept) || !isfinite((double)trace))) atomicOr(g.status, kStatusNoConv);
     double tr = (double)trace;
     if (g.disc && tr > 0) {
       double w = (tr - kept) / tr;
@@ -591,20 +658,21 @@ cudaError_t heevk(cudaStream_t s, int batch, const EigArgs<R>& g) {
   if (g.n > MAXN || g.k > g.n || g.k + 1 > MAXN / 2) return cudaErrorInvalidValue;
   constexpr int NB = 8;  // reflectors per panel (tridiagonalisation and back-transformation)
   const size_t bytes = 2 * sizeof(cplx<R>) * (size_t)NB * g.n + sizeof(R) * (size_t)GB * g.k;
-  static bool attr_set = false;
-  static size_t dyn_max = 0;
-  if (!attr_set) {
+  static PerDevice setup;
+  static size_t dyn_max[kMaxDevices];
+  int dev = 0;
+  cudaError_t e = setup.once([](int d) {
     cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, heevk_kernel<R, NB>);
-    if (e != cudaSuccess) return e;
+    cudaError_t r = cudaFuncGetAttributes(&fa, heevk_kernel<R, NB>);
+    if (r != cudaSuccess) return r;
     const size_t want = 2 * sizeof(cplx<R>) * NB * MAXN + sizeof(R) * GB * (MAXN / 2);
     const size_t cap = 227 * 1024 - fa.sharedSizeBytes;
-    dyn_max = want < cap ? want : cap;
-    e = cudaFuncSetAttribute(heevk_kernel<R, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  if (bytes > dyn_max) return cudaErrorInvalidValue;
+    dyn_max[d] = want < cap ? want : cap;
+    return cudaFuncSetAttribute(heevk_kernel<R, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max[d]);
+  });
+  if (e != cudaSuccess) return e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if (bytes > dyn_max[dev]) return cudaErrorInvalidValue;
   heevk_kernel<R, NB><<<batch, NT, bytes, s>>>(g);
   return cudaGetLastError();
 }

@@ -79,6 +79,7 @@ struct EngBase {
   bool neighbour_trunc = false;  // let 1q gates on a neighbour of the centre skip the centre move
   int64_t purity_limit = 0;      // bytes for the purity chunk buffers, 0 = a share of free memory
   bool tensor_cores = false;     // complex64 products that qualify run on the tcgen05 GEMM
+  int trunc_order = MPDO_TRUNC_SPLIT_FIRST;  // order of the bond split and the Kraus-leg truncation
   // capture snapshot
   std::vector<int> snap_bond, snap_kraus, snap_slot;
   int snap_centre = 0;
@@ -142,6 +143,9 @@ struct EngBase {
   virtual mpdo_status get_site(int chain, int q, double* out) = 0;
   virtual mpdo_status set_site(int q, int dl, int dn, int dr, const double* data) = 0;
   virtual mpdo_status load(FILE* f) = 0;
+  virtual mpdo_status alloc_tc() = 0;
+
+  int* dStatus = nullptr;  // device status word: kStatusNoConv | kStatusTimeout bits set by kernels
 
   mpdo_status sync() {
     cudaError_t e = cudaStreamSynchronize(stream);
@@ -149,6 +153,22 @@ struct EngBase {
       last_err = e;
       return MPDO_ECUDA;
     }
+    return read_status();
+  }
+  // Synchronises, reads the status word and clears it: a bounded wait that ran out is reported as
+  // MPDO_ETIMEOUT, an eigensolver that produced non-finite or collapsed eigenpairs as MPDO_ENOCONV.
+  mpdo_status read_status() {
+    if (!dStatus) return MPDO_OK;
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, dStatus, sizeof(int), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e == cudaSuccess && h) e = cudaMemsetAsync(dStatus, 0, sizeof(int), stream);
+    if (e != cudaSuccess) {
+      last_err = e;
+      return MPDO_ECUDA;
+    }
+    if (h & kStatusTimeout) return MPDO_ETIMEOUT;
+    if (h & kStatusNoConv) return MPDO_ENOCONV;
     return MPDO_OK;
   }
 };
@@ -172,6 +192,12 @@ struct Eng : EngBase {
   ER *wEval = nullptr, *wScr = nullptr;
   C* wSK = nullptr;
   int64_t sSK = 0;
+  C* wHk = nullptr;  // Kraus-first update: the Gram H of Theta0 over (x, r), then the folded gate W
+  int64_t sHk = 0;
+  // complex64: split operand planes of the tensor-core GEMM (floats, all chains); a product whose
+  // planes do not fit runs on the CUDA cores
+  float *tcA = nullptr, *tcB = nullptr;
+  int64_t tcCapA = 0, tcCapB = 0;
   int64_t sEval = 0, sScr = 0;
   double* dDisc = nullptr;  // [B][3]: chi, kappa, gap
   // readout buffers
@@ -184,7 +210,7 @@ struct Eng : EngBase {
 
   ~Eng() override {
     void* ptrs[] = {pool, wQR, wQ, wE, wT, wZ, wF, wU, wH, wY, wX, wK, wRt, wF64, wU64, wEval, wScr, dDisc, wSK,
-                    envL, envR, tmpA, tmpB, dDot, pX, pP, pE, pE2, iota};
+                    envL, envR, tmpA, tmpB, dDot, pX, pP, pE, pE2, iota, dStatus, wHk, tcA, tcB};
     for (void* p : ptrs)
       if (p) cudaFree(p);
   }
@@ -248,6 +274,15 @@ struct Eng : EngBase {
     CK(dmalloc(&tmpA, sTmp * B));
     CK(dmalloc(&tmpB, sTmp * B));
     CK(dmalloc(&dDot, (int64_t)B));
+    if (!std::is_same<R, double>::value) {
+      mpdo_status ts = alloc_tc();
+      if (ts) return ts;
+      tensor_cores = true;
+    }
+    CK(dmalloc(&dStatus, 1));
+    sHk = 16 * K * K;
+    CK(dmalloc(&wHk, sHk * B));
+    CK(cudaMemset(dStatus, 0, sizeof(int)));
     {
       std::vector<int> h(B);
       for (int b = 0; b < B; ++b) h[b] = b;
@@ -257,6 +292,33 @@ struct Eng : EngBase {
     mpdo_status st = reset();
     if (st) return st;
     return sync();
+  }
+
+  // Plane workspaces of the tensor-core GEMM, sized for the largest operands of the update's products
+  // at the caps (per chain; the bond split's F' runs with two batch items per chain).
+  mpdo_status alloc_tc() override {
+    if (std::is_same<R, double>::value || tcA) return MPDO_OK;
+    const int X = chi_max, K = kappa_max;
+    const int shapes[][2] = {{32 * X, 2 * X}, {16 * K, 2 * X * X}, {4 * X, 2 * X}, {2 * K * X, X}, {K * X, 2 * X},
+                             {8 * K * X, X},  {2 * X, K * X},      {8 * X, 2 * X}, {2 * X, 2 * X}, {4 * X, X},
+                             {2 * X * X, 4 * K}, {2 * K * X, 4 * X}, {X, 2 * K * X}, {4 * K, 2 * X * X}};
+    int64_t a = 0, b = 0;
+    for (auto& sh : shapes) {
+      a = lmax(a, tc_plane_floats_a(sh[0], sh[1]));
+      b = lmax(b, tc_plane_floats_b(sh[0], sh[1]));
+    }
+    tcCapA = 2 * a * B;
+    tcCapB = 2 * b * B;
+    cudaError_t e1 = cudaMalloc((void**)&tcA, sizeof(float) * (size_t)tcCapA);
+    cudaError_t e2 = e1 == cudaSuccess ? cudaMalloc((void**)&tcB, sizeof(float) * (size_t)tcCapB) : e1;
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+      if (tcA) cudaFree(tcA);
+      tcA = nullptr;
+      tcCapA = tcCapB = 0;
+      last_err = e1 != cudaSuccess ? e1 : e2;
+      return MPDO_ENOMEM;
+    }
+    return MPDO_OK;
   }
 
   mpdo_status reset() override {
@@ -289,6 +351,11 @@ struct Eng : EngBase {
     g.allow_tc = tensor_cores ? 1 : 0;
     g.ws = wSK;
     g.ws_elems = sSK;
+    g.status = dStatus;
+    g.tc_a = tcA;
+    g.tc_b = tcB;
+    g.tc_a_cap = tcCapA;
+    g.tc_b_cap = tcCapB;
     g.M = M;
     g.N = N;
     g.K = K;
@@ -337,6 +404,7 @@ struct Eng : EngBase {
       a.disc = which >= 0 ? dDisc + which : nullptr;
       a.gap = which >= 0 ? dDisc + 2 : nullptr;
       a.disc_stride = 3;
+      a.status = dStatus;
       prof_start(P_EIG, eig_flops(nmat, k) * B);
       CK(heevk<ER>(stream, B, a));
       prof_stop();
@@ -363,6 +431,7 @@ struct Eng : EngBase {
       a.disc = which >= 0 ? dDisc + which : nullptr;
       a.gap = which >= 0 ? dDisc + 2 : nullptr;
       a.disc_stride = 3;
+      a.status = dStatus;
       prof_start(P_EIG, eig_flops(nmat, k) * B);
       CK(heevk<ER>(stream, B, a));
       prof_stop();
@@ -534,7 +603,7 @@ struct Eng : EngBase {
     st = fuse_(nq, Uhost, Udev, ch, idx);
     if (st) return st;
     if (nq == 2) {
-      st = apply2(q, ch->rpad);
+      st = trunc_order == MPDO_TRUNC_KRAUS_FIRST ? apply2_kraus_first(q, ch->rpad) : apply2(q, ch->rpad);
       dirty = -1;
       return st;
     }
@@ -689,6 +758,93 @@ struct Eng : EngBase {
     const int kap = imin(kappa_max, imin((int)Lx, NK));
     const int s2 = take_slot();
     st = kappa_truncate_X(NK, S, dr, kap, s2);
+    if (st) return st;
+    give_slot(site_slot[q]);
+    give_slot(site_slot[q + 1]);
+    site_slot[q] = s1;
+    site_slot[q + 1] = s2;
+    bond[q + 1] = kchi;
+    kraus[q + 1] = kap;
+    centre = q + 1;
+    return MPDO_OK;
+  }
+
+  // Two-qubit update in the Kraus-first order: the merged tensor's new Kraus leg (k, n2) is truncated to
+  // kappa_max (Eq. svdNoise) before the bond split (Fig. 3b).  Theta is never formed: with
+  // Theta0 = R1 A2 (the pair reduced by the QR of A1), the leg's Gram is assembled from the small Gram
+  // H of Theta0 over (x, r) and the fused gate, the kept directions are folded into the gate
+  // (W = sum_k Khat_k V_k), and Theta' = W Theta0 carries kappa instead of r_k kappa Kraus indices
+  // into the split.  The centre ends on q + 1.
+  mpdo_status apply2_kraus_first(int q, int rk) {
+    const int dl = bond[q], dm = bond[q + 1], dr = bond[q + 2];
+    const int dn1 = kraus[q], dn2 = kraus[q + 1];
+    const int C2 = 2 * dm;
+    // 1. QR of A1 as ((l, n1), (p1, b)) -> Q1 (m x x, wQ), R1 (x x 2dm, wQR), column-major ld m
+    const int m = dl * dn1, x = imin(m, C2);
+    QrArgs<R> qa;
+    qa.m = m;
+    qa.n = C2;
+    qa.in = site_ptr(q);
+    qa.vin = v2(slot_elems, dn1, (int64_t)2 * dn1 * dm, dm, dm, (int64_t)dn1 * dm, 1);
+    qa.W = wQR;
+    qa.wstride = sQR;
+    qa.Qw = wQ;
+    qa.qstride = sQR;
+    qa.qout = nullptr;
+    prof_start(P_QR, qr_flops(qa.m, qa.n) * B);
+    CK(qr<R>(stream, B, qa));
+    prof_stop();
+    ++launches;
+    // 2. Theta0[(x, p1)][(p2, n2, r)] = sum_bb R1[x, (p1, bb)] A2[bb][(p2, n2, r)]  (wX)
+    const int N0 = 2 * dn2 * dr;
+    mpdo_status st = gemm_(2 * x, N0, dm, wQR, v2(sQR, 2, 1, (int64_t)dm * m, 0, 0, m), site_ptr(q + 1),
+                           row_major(N0, slot_elems), wX, row_major(N0, sX));
+    if (st) return st;
+    // 3. H[(p, n2), (p'', n2')] = sum_{x, r} conj(Theta0[x, p, n2, r]) Theta0[x, p'', n2', r]  (wHk, row-major)
+    const int NH = 4 * dn2;
+    const int64_t ld0 = (int64_t)4 * dn2 * dr;  // stride of x in Theta0
+    st = gemm_(NH, NH, x * dr, wX, v2(sX, 0, 0, dr, dr, ld0, 1, 1), wX, v2(sX, dr, ld0, 1, 0, 0, dr), wHk,
+               row_major(NH, sHk));
+    if (st) return st;
+    // 4. the Kraus-leg Gram G (rk dn2 square, column-major, wF) and its top-kappa eigenpairs
+    const int NK = rk * dn2;
+    prof_start(P_OTHER, 8.0 * NK * NK * 80 * B);
+    CK(kraus_gram<R>(stream, B, rk, dn2, wK, wHk, sHk, wF, sF));
+    prof_stop();
+    ++launches;
+    const int kap = imin(kappa_max, imin(NK, x * 4 * dr));
+    st = eig_(NK, kap, 1);
+    if (st) return st;
+    // 5. W[(p', nu), (p, n2)] = sum_k Khat_k[p', p] V[(k, n2), nu]  (wHk, row-major 4 kap x 4 dn2)
+    prof_start(P_OTHER, 8.0 * 16 * kap * dn2 * rk * B);
+    CK(kraus_fold<R>(stream, B, rk, dn2, kap, wK, wU, sU, NK, wHk, sHk));
+    prof_stop();
+    ++launches;
+    // 6. Theta'[x][(p1', p2')][nu][r] = sum_{(p, n2)} W[(p', nu), (p, n2)] Theta0[x][(p, n2)][r]  (wY)
+    st = gemm_(4 * kap, x * dr, NH, wHk, row_major(NH, sHk), wX, v2(sX, 0, 0, dr, dr, ld0, 1), wY,
+               v2(sY, 0, 0, dr, dr, (int64_t)4 * kap * dr, 1));
+    if (st) return st;
+    // 7. F[(x, p1'), (x', p1'')] = sum_{(p2', nu, r)} Theta' conj(Theta')  (wF, column-major, Hermitian)
+    const int NF = 2 * x, KF = 2 * kap * dr;
+    st = gemm_(NF, NF, KF, wY, row_major(KF, sY), wY, v2(sY, 0, 0, 1, 0, 0, KF, 1), wF, col_major(NF, sF), -1, 1);
+    if (st) return st;
+    prof_start(P_OTHER, 0);
+    CK(herm_fill_upper<R>(stream, B, NF, wF, sF));
+    prof_stop();
+    ++launches;
+    // 8. bond: top kchi eigenpairs of F
+    const int kchi = imin(chi_max, imin(NF, KF));
+    st = eig_(NF, kchi, 0);
+    if (st) return st;
+    // 9. A1' [l][p1'][n1][b'] = sum_x Q1[(l, n1), x] U[(x, p1'), b']
+    const int s1 = take_slot();
+    st = gemm_(m, 2 * kchi, x, wQ, col_major(m, sQR), wU, v2(sU, 0, 0, 2, kchi, 1, (int64_t)2 * x),
+               slot_ptr(s1), v2(slot_elems, dn1, (int64_t)2 * dn1 * kchi, kchi, kchi, (int64_t)dn1 * kchi, 1));
+    if (st) return st;
+    // 10. A2'[b'][(p2', nu, r)] = sum_{(x, p1')} conj(U[(x, p1'), b']) Theta'[(x, p1'), (p2', nu, r)]
+    const int s2 = take_slot();
+    st = gemm_(kchi, KF, NF, wU, v2(sU, 0, 0, NF, 0, 0, 1, 1), wY, row_major(KF, sY), slot_ptr(s2),
+               row_major(KF, slot_elems));
     if (st) return st;
     give_slot(site_slot[q]);
     give_slot(site_slot[q + 1]);
@@ -862,8 +1018,11 @@ struct Eng : EngBase {
       if (st) return st;
       std::swap(Ea, Eb);
     }
+    // element [0, 0] of every chain's environment gathered into one contiguous buffer, one copy
     std::vector<C> hc(B);
-    for (int b = 0; b < B; ++b) CK(cudaMemcpyAsync(&hc[b], Ea + (int64_t)b * sEnv, sizeof(C), cudaMemcpyDeviceToHost, stream));
+    CK(copy_view<R>(stream, B, 1, 1, Ea, v2(sEnv, 0, 0, 1, 0, 0, 1), tmpB, row_major(1, 1)));
+    ++launches;
+    CK(cudaMemcpyAsync(hc.data(), tmpB, sizeof(C) * B, cudaMemcpyDeviceToHost, stream));
     CK(cudaStreamSynchronize(stream));
     re.resize(B);
     im.resize(B);
@@ -980,6 +1139,10 @@ struct Eng : EngBase {
 
   mpdo_status expect(int kind, const int* args, int nargs, double* out) override {
     if (capturing) return MPDO_ESTATE;
+    {
+      mpdo_status ss = read_status();
+      if (ss) return ss;
+    }
     if (kind == MPDO_EXPECT_DISCARDED) {
       CK(cudaMemcpyAsync(out, dDisc, sizeof(double) * 3 * B, cudaMemcpyDeviceToHost, stream));
       CK(cudaStreamSynchronize(stream));
@@ -1201,7 +1364,7 @@ const char* mpdo_status_string(int s) {
     case MPDO_ENOMEM: return "out of memory";
     case MPDO_ENOTCP: return "process matrix is not completely positive";
     case MPDO_ENOTTP: return "process matrix is not trace preserving";
-    case MPDO_ENOCONV: return "non-finite result";
+    case MPDO_ENOCONV: return "eigensolver or readout produced a non-finite or collapsed result";
     case MPDO_ETIMEOUT: return "timeout";
     case MPDO_ECUDA: return "CUDA error";
     case MPDO_ESTATE: return "invalid state for this call";
@@ -1584,7 +1747,18 @@ mpdo_status mpdo_set_centre(mpdo_t h, int q) {
 
 mpdo_status mpdo_set_tensor_cores(mpdo_t h, int enable) {
   if (!h) return MPDO_EINVAL;
+  if (enable && h->e->prec != MPDO_FP64) {
+    if (h->e->capturing) return MPDO_ESTATE;
+    mpdo_status st = h->e->alloc_tc();
+    if (st) return st;
+  }
   h->e->tensor_cores = enable != 0;
+  return MPDO_OK;
+}
+
+mpdo_status mpdo_set_trunc_order(mpdo_t h, int order) {
+  if (!h || (order != MPDO_TRUNC_SPLIT_FIRST && order != MPDO_TRUNC_KRAUS_FIRST)) return MPDO_EINVAL;
+  h->e->trunc_order = order;
   return MPDO_OK;
 }
 

@@ -10,12 +10,12 @@
 // outside the matrix) through a STAGES-deep ring of k-tiles of 16, so loads for later k-tiles are in
 // flight while the current one is multiplied, without staging registers.  The per-row (A) and
 // per-column (B) view offsets of the tile are computed once into shared memory.
-// FP32 reductions with K >= 128 (every contraction of a two-qubit update and the Gram matrices of the
-// truncations) sum each k-tile into a fresh partial and add it to the running value with Knuth's
-// TwoSum, so their rounding error does not grow with K; shorter products accumulate directly.
+// FP32 reductions sum each k-tile into a fresh partial and add it to the running value with Knuth's
+// TwoSum, so their rounding error does not grow with K.
 // Long reductions whose output has too few tiles to fill the GPU (the Kraus-leg Grams: 128 x 128
 // or 32 x 32 per chain over 8192 rows) are split along K over several CTAs; each writes its partial
 // tile to a workspace and a second kernel adds the partials in FP64 and applies alpha and beta.
+#include "device_once.cuh"
 #include "kernels.h"
 
 namespace mpdo {
@@ -254,17 +254,15 @@ cudaError_t launch(cudaStream_t s, int batch, const GemmArgs<R>& g) {
   // three stages for complex64, two for complex128 (twice the bytes per element)
   constexpr int STAGES = sizeof(R) == 4 ? 3 : 2;
   constexpr size_t bytes = smem_bytes<R, TMR, TNC, STAGES>();
-  static bool attr_set = false;
-  static int n_sm = 0;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_kernel<R, COMP, TMR, TNC, STAGES>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  static PerDevice setup;
+  {
+    cudaError_t e = setup.once([](int) {
+      return cudaFuncSetAttribute(gemm_kernel<R, COMP, TMR, TNC, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)bytes);
+    });
     if (e != cudaSuccess) return e;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0) n_sm = 1;
-    attr_set = true;
   }
+  const int n_sm = sm_count();
   const int a_m_fast = (g.va.rdiv == 0 && g.va.rlo == 1) ? 1 : 0;
   const int b_n_fast = (g.vb.cdiv == 0 && g.vb.clo == 1) ? 1 : 0;
   const int tm = (g.M + BM - 1) / BM, tn = (g.N + BN - 1) / BN;
@@ -311,14 +309,11 @@ cudaError_t gemm(cudaStream_t s, int batch, const GemmArgs<R>& g) {
   const bool small = g.M <= 32 && g.N <= 32;
   const bool wide = g.M <= 16 && g.N > 32 && !g.herm;
   if constexpr (sizeof(R) == 4) {
-    if (g.allow_tc && g.K <= 2048 && tc_gemm_applicable(g)) return tc_gemm(s, batch, g);
-    if (g.K >= 128) {
-      if (wide) return launch<R, true, 1, 8>(s, batch, g);
-      return small ? launch<R, true, 2, 2>(s, batch, g) : launch<R, true, 4, 4>(s, batch, g);
-    }
-    if (wide) return launch<R, false, 1, 8>(s, batch, g);
-    if (g.M > 64 && !g.herm) return launch<R, false, 8, 4>(s, batch, g);
-    return small ? launch<R, false, 2, 2>(s, batch, g) : launch<R, false, 4, 4>(s, batch, g);
+    if (g.allow_tc && tc_gemm_applicable(g, batch)) return tc_gemm(s, batch, g);
+    // every FP32 product sums its k-tiles with TwoSum: the stored complex64 state is rounded at
+    // every step anyway, and uncompensated sums of even 64 terms added measurably to it
+    if (wide) return launch<R, true, 1, 8>(s, batch, g);
+    return small ? launch<R, true, 2, 2>(s, batch, g) : launch<R, true, 4, 4>(s, batch, g);
   } else {
     if (wide) return launch<R, false, 1, 8>(s, batch, g);
     return small ? launch<R, false, 2, 2>(s, batch, g) : launch<R, false, 4, 4>(s, batch, g);

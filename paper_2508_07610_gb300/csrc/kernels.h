@@ -23,14 +23,26 @@ struct GemmArgs {
   // nullptr disables splitting
   cplx<R>* ws = nullptr;
   int64_t ws_elems = 0;
+  int* status = nullptr;  // nullable: kStatusTimeout is or-ed in when a bounded wait runs out
+  // complex64 only: workspaces for the tensor-core GEMM's split operand planes (floats, all batch
+  // items); nullptr keeps every product on the CUDA cores
+  float* tc_a = nullptr;
+  float* tc_b = nullptr;
+  int64_t tc_a_cap = 0, tc_b_cap = 0;
 };
+
+// bits of a handle's device status word (read and cleared by the host at synchronising calls)
+constexpr int kStatusNoConv = 1;   // an eigensolver produced non-finite or collapsed eigenpairs
+constexpr int kStatusTimeout = 2;  // a bounded wait inside a kernel ran out
 template <typename R>
 cudaError_t gemm(cudaStream_t s, int batch, const GemmArgs<R>& g);
 
-// tensor-core (tcgen05, split TF32) complex64 GEMM; applicable to non-Hermitian M >= 128 products
-bool tc_gemm_applicable(const GemmArgs<float>& g);
+// tensor-core (tcgen05, split TF32, compensated folding) complex64 GEMM for products with M >= 128,
+// N >= 64, K >= 16 whose split planes fit the workspaces; plane sizes in floats per batch item
+bool tc_gemm_applicable(const GemmArgs<float>& g, int batch);
 cudaError_t tc_gemm(cudaStream_t s, int batch, const GemmArgs<float>& g);
-int tc_gemm_error_flag();
+int64_t tc_plane_floats_a(int M, int K);
+int64_t tc_plane_floats_b(int N, int K);
 
 template <typename R>
 struct QrArgs {
@@ -61,6 +73,7 @@ struct EigArgs {
   double* disc;     // nullable: += (trace - sum of kept) / trace
   double* gap;      // nullable: min((w_{k-1} - w_k) / w_0)
   int64_t disc_stride;
+  int* status = nullptr;  // nullable: kStatusNoConv is or-ed in on a non-finite or collapsed result
 };
 template <typename R>
 cudaError_t heevk(cudaStream_t s, int batch, const EigArgs<R>& g);
@@ -103,6 +116,17 @@ cudaError_t build_T(cudaStream_t s, int batch, int dm, const cplx<R>* Rt, const 
 template <typename R>
 cudaError_t build_Y(cudaStream_t s, int batch, int kchi, int dm, int rk, const cplx<R>* Khat, const cplx<R>* H,
                     int64_t hstride, cplx<R>* Y, int64_t ystride);
+
+// Kraus-first two-qubit update: the Kraus-leg Gram of Theta = (Khat (x) I) Theta0 from the Gram H of
+// Theta0, G[(k, n), (k', n')] = sum_{p, p''} (Khat_k^H Khat_k')[p, p''] H[(p, n), (p'', n')]
+// (G column-major rk dn square, H row-major 4 dn square), and the kept directions V (column-major,
+// ld vld) folded into the gate, W[(p', nu), (p, n)] = sum_k Khat_k[p', p] V[(k, n), nu] (row-major).
+template <typename R>
+cudaError_t kraus_gram(cudaStream_t s, int batch, int rk, int dn, const cplx<R>* Khat, const cplx<R>* H,
+                       int64_t hstride, cplx<R>* G, int64_t gstride);
+template <typename R>
+cudaError_t kraus_fold(cudaStream_t s, int batch, int rk, int dn, int kap, const cplx<R>* Khat, const cplx<R>* V,
+                       int64_t vstride, int vld, cplx<R>* W, int64_t wstride);
 
 // out(view) = in(view) for an M x N block, optional per-row scale by a diagonal d[row % dmod]
 template <typename R>

@@ -188,6 +188,51 @@ __global__ void build_Y_kernel(int kchi, int dm, int rk, const cplx<R>* Khat, co
   }
 }
 
+// Kraus-leg Gram of the merged two-site tensor, Theta = (Khat (x) I) Theta0, from the Gram H of Theta0
+// over (x, r):  G[(k, n), (k', n')] = sum_{p, p''} M_kk'[p, p''] H[(p, n), (p'', n')] with
+// M_kk' = Khat_k^H Khat_k' (4 x 4); G column-major (ld rk dn), H row-major (4 dn x 4 dn).
+template <typename R>
+__global__ void kraus_gram_kernel(int rk, int dn, const cplx<R>* Khat, const cplx<R>* H, int64_t hstride,
+                                  cplx<R>* G, int64_t gstride) {
+  const int z = blockIdx.y;
+  const int NK = rk * dn, NH = 4 * dn;
+  const cplx<R>* K = Khat + (int64_t)z * rk * 16;
+  const cplx<R>* Hz = H + (int64_t)z * hstride;
+  cplx<R>* Gz = G + (int64_t)z * gstride;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)NK * NK;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(e % NK), b = (int)(e / NK);
+    const int k = a / dn, n = a % dn, k2 = b / dn, n2 = b % dn;
+    cplx<R> acc = mk<R>(0, 0);
+    for (int p = 0; p < 4; ++p)
+      for (int pp = 0; pp < 4; ++pp) {
+        cplx<R> m = mk<R>(0, 0);
+        for (int t = 0; t < 4; ++t) cfma_cj(m, K[k * 16 + t * 4 + p], K[k2 * 16 + t * 4 + pp]);
+        cfma(acc, m, Hz[(int64_t)(p * dn + n) * NH + pp * dn + n2]);
+      }
+    Gz[e] = acc;
+  }
+}
+
+// The kept Kraus directions folded into the fused gate:
+//   W[(p', nu), (p, n)] = sum_k Khat_k[p', p] V[(k, n), nu]   (row-major 4 kap x 4 dn; V column-major, ld vld)
+template <typename R>
+__global__ void kraus_fold_kernel(int rk, int dn, int kap, const cplx<R>* Khat, const cplx<R>* V, int64_t vstride,
+                                  int vld, cplx<R>* W, int64_t wstride) {
+  const int z = blockIdx.y;
+  const int rows = 4 * kap, cols = 4 * dn;
+  const cplx<R>* K = Khat + (int64_t)z * rk * 16;
+  const cplx<R>* Vz = V + (int64_t)z * vstride;
+  cplx<R>* Wz = W + (int64_t)z * wstride;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < rows * cols; e += gridDim.x * blockDim.x) {
+    const int i = e / cols, j = e % cols;
+    const int pq = i / kap, nu = i % kap, p = j / dn, n = j % dn;
+    cplx<R> acc = mk<R>(0, 0);
+    for (int k = 0; k < rk; ++k) cfma(acc, K[k * 16 + pq * 4 + p], Vz[(int64_t)(k * dn + n) + (int64_t)nu * vld]);
+    Wz[e] = acc;
+  }
+}
+
 template <typename R>
 __global__ void copy_view_kernel(int M, int N, const cplx<R>* in, View vin, cplx<R>* out, View vout) {
   const int z = blockIdx.y;
@@ -376,6 +421,24 @@ cudaError_t build_Y(cudaStream_t s, int batch, int kchi, int dm, int rk, const c
   return cudaGetLastError();
 }
 template <typename R>
+cudaError_t kraus_gram(cudaStream_t s, int batch, int rk, int dn, const cplx<R>* Khat, const cplx<R>* H,
+                       int64_t hstride, cplx<R>* G, int64_t gstride) {
+  if (batch <= 0) return cudaSuccess;
+  if (rk > 16) return cudaErrorInvalidValue;
+  dim3 grid(grid_for((int64_t)rk * dn * rk * dn), batch);
+  kraus_gram_kernel<R><<<grid, NT, 0, s>>>(rk, dn, Khat, H, hstride, G, gstride);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t kraus_fold(cudaStream_t s, int batch, int rk, int dn, int kap, const cplx<R>* Khat, const cplx<R>* V,
+                       int64_t vstride, int vld, cplx<R>* W, int64_t wstride) {
+  if (batch <= 0) return cudaSuccess;
+  if (rk > 16) return cudaErrorInvalidValue;
+  dim3 grid(grid_for((int64_t)16 * kap * dn), batch);
+  kraus_fold_kernel<R><<<grid, NT, 0, s>>>(rk, dn, kap, Khat, V, vstride, vld, W, wstride);
+  return cudaGetLastError();
+}
+template <typename R>
 cudaError_t copy_view(cudaStream_t s, int batch, int M, int N, const cplx<R>* in, View vin, cplx<R>* out, View vout) {
   if (batch <= 0 || M <= 0 || N <= 0) return cudaSuccess;
   dim3 grid(grid_for((int64_t)M * N), batch);
@@ -446,6 +509,10 @@ cudaError_t permute(cudaStream_t s, int batch, int nd, const int* dims, const in
   template cudaError_t build_Y<R>(cudaStream_t, int, int, int, int, const cplx<R>*, const cplx<R>*, int64_t,     \
                                   cplx<R>*, int64_t);                                                            \
   template cudaError_t copy_view<R>(cudaStream_t, int, int, int, const cplx<R>*, View, cplx<R>*, View);          \
+  template cudaError_t kraus_gram<R>(cudaStream_t, int, int, int, const cplx<R>*, const cplx<R>*, int64_t,       \
+                                     cplx<R>*, int64_t);                                                         \
+  template cudaError_t kraus_fold<R>(cudaStream_t, int, int, int, int, const cplx<R>*, const cplx<R>*, int64_t,  \
+                                     int, cplx<R>*, int64_t);                                                    \
   template cudaError_t scale_odd<R>(cudaStream_t, int, int64_t, int64_t, R, cplx<R>*, int64_t);                  \
   template cudaError_t init_zero_sites<R>(cudaStream_t, int, cplx<R>*, int64_t);                                 \
   template cudaError_t dot_batch<R>(cudaStream_t, int, int64_t, const cplx<R>*, int64_t, const cplx<R>*,         \

@@ -28,29 +28,53 @@ static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 std::mutex g_mu;
 double* g_ptr[64] = {nullptr};  // device address of g_noalloc_scratch, per device ordinal
 
+// Kraus operators of channel c from its Choi eigenpairs (descending), pruned at tol * max eta.  The
+// rank written is -1 when the negative Choi mass exceeds 1e-8 (not completely positive) and -2 when
+// sum_i K_i^H K_i differs from I by more than 1e-8 (not trace preserving); the operators are then zero.
 __global__ void prune_and_build_kraus(int count, int nq, double tol, const double* eta, const cplx<double>* vecs,
                                       cplx<double>* kraus, int* ranks) {
   const int c = blockIdx.x;
   if (c >= count) return;
   const int d = 1 << nq, d2 = d * d;
   const double* w = eta + (int64_t)c * d2;
-  __shared__ int s_r;
+  cplx<double>* K = kraus + (int64_t)c * d2 * d2;
+  __shared__ int s_r, s_bad;
   if (threadIdx.x == 0) {
-    double emax = w[0] > 0 ? w[0] : 0;
+    double emax = w[0] > 0 ? w[0] : 0, neg = 0;
     int r = 0;
-    for (int i = 0; i < d2; ++i)
+    for (int i = 0; i < d2; ++i) {
       if (w[i] > tol * emax && w[i] > 0) ++r;
+      if (w[i] < 0) neg -= w[i];
+    }
     if (r < 1) r = 1;
     s_r = r;
-    ranks[c] = r;
+    s_bad = (neg > 1e-8 || !(neg == neg)) ? -1 : 0;
   }
   __syncthreads();
   for (int e = threadIdx.x; e < d2 * d2; e += blockDim.x) {
     int i = e / d2, a = e % d2;
     cplx<double> v = mk<double>(0, 0);
-    if (i < s_r) v = sqrt(fmax(w[i], 0.0)) * vecs[(int64_t)c * d2 * d2 + a + (int64_t)i * d2];
-    kraus[(int64_t)c * d2 * d2 + e] = v;
+    if (i < s_r && !s_bad) v = sqrt(fmax(w[i], 0.0)) * vecs[(int64_t)c * d2 * d2 + a + (int64_t)i * d2];
+    K[e] = v;
   }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (!s_bad) {
+      double err = 0;
+      for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b) {
+          cplx<double> t = mk<double>(a == b ? -1.0 : 0.0, 0.0);
+          for (int i = 0; i < s_r; ++i)
+            for (int m = 0; m < d; ++m) t = t + conjg(K[i * d2 + m * d + a]) * K[i * d2 + m * d + b];
+          err = fmax(err, sqrt(norm2(t)));
+        }
+      if (!(err <= 1e-8)) s_bad = -2;
+    }
+    ranks[c] = s_bad ? s_bad : s_r;
+  }
+  __syncthreads();
+  if (s_bad)
+    for (int e = threadIdx.x; e < d2 * d2; e += blockDim.x) K[e] = mk<double>(0, 0);
 }
 
 // Device address of the scratch array for the current device (set up once per device).

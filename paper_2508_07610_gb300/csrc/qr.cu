@@ -11,6 +11,7 @@
 // Reflectors are H = I - beta v v^H with v = y + e^{i arg y0} |y| e_0, so H y = -e^{i arg y0} |y| e_0.
 #include <cooperative_groups.h>
 
+#include "device_once.cuh"
 #include "kernels.h"
 #include "panel.cuh"
 
@@ -497,13 +498,11 @@ __global__ void __launch_bounds__(NT) qr_blocked_kernel(QrArgs<R> g) {
 
 template <typename R, int NB>
 cudaError_t launch_blocked(cudaStream_t s, int batch, const QrArgs<R>& g, size_t bytes) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e =
-        cudaFuncSetAttribute(qr_blocked_kernel<R, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static PerDevice setup;
+  cudaError_t e = setup.once([](int) {
+    return cudaFuncSetAttribute(qr_blocked_kernel<R, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  });
+  if (e != cudaSuccess) return e;
   qr_blocked_kernel<R, NB><<<batch, NT, bytes, s>>>(g);
   return cudaGetLastError();
 }
@@ -523,24 +522,18 @@ cudaError_t qr(cudaStream_t s, int batch, const QrArgs<R>& g) {
   // Few matrices (latency-bound): the smallest cluster (2, 4 or 8 CTAs) whose shared memory holds the
   // matrix.  Many matrices (throughput-bound): one CTA per matrix, which keeps every SM busy with
   // several small-footprint CTAs and spends fewer SM-cycles per factorisation.
-  static int n_sm = 0;
-  if (n_sm == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0) n_sm = 1;
-  }
+  const int n_sm = sm_count();
   for (int C = 2; C <= 8; C *= 2) {
     int mloc = (g.m + C - 1) / C;
     size_t bytes = cluster_smem_bytes<R>(mloc, g.n);
     if (bytes > kClusterSmemBudget || g.m < 2 * C) continue;
     if ((int64_t)batch * C > n_sm) break;
-    static bool attr_set = false;
-    if (!attr_set) {
-      cudaError_t e = cudaFuncSetAttribute(qr_cluster_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)kClusterSmemBudget);
-      if (e != cudaSuccess) return e;
-      attr_set = true;
-    }
+    static PerDevice setup;
+    cudaError_t ea = setup.once([](int) {
+      return cudaFuncSetAttribute(qr_cluster_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kClusterSmemBudget);
+    });
+    if (ea != cudaSuccess) return ea;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(batch * C));
     cfg.blockDim = dim3(NT);

@@ -11,13 +11,14 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include "device_once.cuh"
 #include "surrogate_tc.h"
+#include "wait.cuh"
 
 namespace surr_tc {
 
 namespace {
 constexpr int TM = 128, NTH = 128, STAGES = 2, KC = 64;
-constexpr long long kWaitLimit = 1ll << 26;
 
 __device__ int g_fail = 0;
 
@@ -45,18 +46,7 @@ __device__ __forceinline__ uint32_t instr_desc(int n) {
   return d;
 }
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (long long it = 0; it < kWaitLimit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.b32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done)
-        : "r"(mbar), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
+  return mpdo::mbar_wait_bounded(mbar, parity);
 }
 
 // byte offset of the 16-byte chunk (row, c8) of a rows x kc K-major tile (c8 = k / 8)
@@ -183,14 +173,13 @@ cudaError_t linear(cudaStream_t s, int Bn, int O, int I, const __nv_bfloat16* ac
   int ncols = 32;  // TMEM columns: a power of two >= 32 that holds O
   while (ncols < O) ncols *= 2;
   const int bytes = STAGES * (TM * KC * 2 + ncols * KC * 2) + 256;
-  static bool attr = false;
-  if (!attr) {
+  static mpdo::PerDevice setup;
+  cudaError_t e = setup.once([](int) {
     // at most 97 KB per CTA at O = 256: two CTAs per SM hold 2 x 256 of the 512 TMEM columns
-    cudaError_t e = cudaFuncSetAttribute(linear_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         STAGES * (TM * KC * 2 + 256 * KC * 2) + 256);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+    return cudaFuncSetAttribute(linear_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                STAGES * (TM * KC * 2 + 256 * KC * 2) + 256);
+  });
+  if (e != cudaSuccess) return e;
   linear_kernel<<<(Bn + TM - 1) / TM, NTH, bytes, s>>>(Bn, O, I, act, W, Z, ncols);
   return cudaGetLastError();
 }

@@ -69,6 +69,9 @@ def lib():
         "mpdo_set_tensor_cores": [vp, i32],
         "mpdo_set_purity_memory": [vp, C.c_longlong],
         "mpdo_profile_read": [vp, dp, dp, C.POINTER(C.c_longlong)],
+        "mpdo_wait_selftest": [i32, ip],
+        "mpdo_set_trunc_order": [vp, i32],
+        "mpdo_tc_selftest": [i32, i32, i32, dp, ip],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -222,6 +225,13 @@ class MPDO:
     def set_purity_memory(self, nbytes: int):
         _check(lib().mpdo_set_purity_memory(self.h, C.c_longlong(nbytes)), "mpdo_set_purity_memory")
 
+    TRUNC_ORDERS = {"split_first": 0, "kraus_first": 1}
+
+    def set_trunc_order(self, order: str):
+        """'split_first' (bond split, then the Kraus leg of q+1) or 'kraus_first' (the merged tensor's
+        new Kraus leg first, then the split), for every later apply_2q."""
+        _check(lib().mpdo_set_trunc_order(self.h, self.TRUNC_ORDERS[order]), "mpdo_set_trunc_order")
+
     def set_neighbour_truncation(self, enable: bool):
         _check(lib().mpdo_set_neighbour_truncation(self.h, 1 if enable else 0), "mpdo_set_neighbour_truncation")
 
@@ -329,9 +339,27 @@ class MPDO:
         return Graph(g)
 
 
-def run_circuit(circuit, chi_max: int, kappa_max: int, prec="fp64", stream: int = 0) -> MPDO:
+def tc_selftest(M: int, N: int, K: int):
+    """Random complex64 M x K times K x N on the tensor cores and on the CUDA cores: returns (largest
+    entry-wise difference relative to the largest entry, the tensor-core kernel's status word)."""
+    err, flag = C.c_double(), C.c_int()
+    _check(lib().mpdo_tc_selftest(M, N, K, C.byref(err), C.byref(flag)), "mpdo_tc_selftest")
+    return err.value, flag.value
+
+
+def wait_selftest(limit_us: int):
+    """Run the bounded-wait probe (a wait on an mbarrier that nothing arrives on); returns
+    (status, device status word).  Status 6 (timeout) is the expected outcome."""
+    word = C.c_int(0)
+    st = lib().mpdo_wait_selftest(int(limit_us), C.byref(word))
+    return st, word.value
+
+
+def run_circuit(circuit, chi_max: int, kappa_max: int, prec="fp64", stream: int = 0,
+                trunc_order: str = "split_first") -> MPDO:
     """Apply a workloads.Circuit on one chain; each channel is converted on the GPU once."""
     st = MPDO(circuit.n, chi_max, kappa_max, prec, 1, stream)
+    st.set_trunc_order(trunc_order)
     chans = {}
     for op in circuit.ops:
         ch = chans.get(op.chan)

@@ -339,3 +339,31 @@ def test_neighbour_truncation_layer_pattern():
                 gate(2, q, False)
             gate(1, 0, False)
     _check_state(st, orc, "fp64", n, label="neighbour layer pattern")
+
+
+# ------------------------------------------------------------------ truncation order (Sec. II.D schedules)
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp32"])
+@pytest.mark.parametrize("case", ["ghz", "random5", "random6"])
+def test_kraus_first_order_matches_oracle(prec, case):
+    """MPDO_TRUNC_KRAUS_FIRST: the merged tensor's new Kraus leg is truncated before the bond split, on
+    the GPU through the Gram of the reduced pair (Theta is never formed), in the oracle by an explicit
+    SVD of the merged tensor."""
+    if case == "ghz":
+        circ, chi, kap = W.ghz_ansatz(), 16, 4
+    else:
+        n = int(case[-1])
+        rng = np.random.default_rng(700 + n)
+        circ, chi, kap = W.random_circuit(n, 24, rng, rank1=3, rank2=6), 5, 3
+    st = G.run_circuit(circ, chi, kap, prec, trunc_order="kraus_first")
+    orc = OM.run_circuit(circ, chi, kap, trunc_order="kraus_first")
+    _check_state(st, orc, prec, circ.n, label=f"kraus_first {case}")
+
+
+def test_kraus_first_equals_split_first_without_bond_cuts():
+    rng = np.random.default_rng(91)
+    circ = W.random_circuit(4, 16, rng, rank1=3, rank2=6)
+    a = G.run_circuit(circ, 64, 3, "fp64", trunc_order="split_first")
+    b = G.run_circuit(circ, 64, 3, "fp64", trunc_order="kraus_first")
+    ra, rb = _oracle_from_gpu(a).dense(), _oracle_from_gpu(b).dense()
+    assert np.max(np.abs(ra / np.trace(ra) - rb / np.trace(rb))) < 1e-12
+    assert abs(a.discarded()[0, 1] - b.discarded()[0, 1]) < 1e-12
