@@ -65,6 +65,8 @@ def run_circuit(circuit) -> np.ndarray:
     n = circuit.n
     rho = zero_state(n)
     for op in circuit.ops:
+        if op.kind == 3:  # a bond-truncation directive: the exact state is left as it is
+            continue
         nq, chi = circuit.chis[op.chan]
         qs = [op.q] if op.kind == 1 else [op.q, op.q + 1]
         rho = apply_noisy_gate(rho, n, qs, op.U, chi)
@@ -108,3 +110,21 @@ def maxcut_expectation(rho, n, edges) -> float:
 
 def probabilities(rho) -> np.ndarray:
     return np.real(np.diag(rho)) / trace(rho)
+
+
+def _psd_sqrt(rho: np.ndarray) -> np.ndarray:
+    """The positive square root of a Hermitian PSD matrix through its eigendecomposition (negative
+    rounding-level eigenvalues clipped to 0)."""
+    w, V = np.linalg.eigh((rho + rho.conj().T) / 2)
+    return (V * np.sqrt(np.clip(w, 0.0, None))) @ V.conj().T
+
+
+def uhlmann_fidelity(rho: np.ndarray, sigma: np.ndarray) -> float:
+    """F(rho, sigma) = (tr sqrt(sqrt(rho) sigma sqrt(rho)))^2 (Sec. IV.C, Eq. fidelity), both states
+    normalised to unit trace first (the MPDO keeps the trace that truncation removed)."""
+    r = rho / np.trace(rho).real
+    s = sigma / np.trace(sigma).real
+    sr = _psd_sqrt(r)
+    M = sr @ s @ sr
+    w = np.linalg.eigvalsh((M + M.conj().T) / 2)
+    return float(np.sum(np.sqrt(np.clip(w, 0.0, None))) ** 2)

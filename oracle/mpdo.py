@@ -14,6 +14,9 @@ Steps, in the paper's order:
     and the two-site tensor is split by an SVD that keeps the top chi_max values;
   * Kraus-leg truncation (Eq. svdNoise, Fig. 3a): the site tensor as a
     (p, l, r) x n matrix is SVD-truncated to kappa_max values, T' = U S (= T V).
+  * the paper's global schedule (Sec. II.D): QR decompositions from left to right into canonical
+    form, then an SVD truncation of every bond from right to left (truncate_bonds, run where a
+    circuit places a SWEEP op).
 Readings where the paper is silent: truncation runs per gate with the
 orthogonality centre on the touched site (either site of a two-qubit gate); after a two-qubit gate the bond is
 split first and the right site's Kraus leg truncated second (trunc_order "split_first"; the order
@@ -138,6 +141,28 @@ class MPDO:
         self.discarded_kappa += w
         self.log.append(("kappa", q, k, len(s), w))
         return w
+
+    def truncate_bonds(self, chi: int) -> float:
+        """The global bond truncation of Sec. II.D (Fig. 3b): QR decompositions from left to right
+        bring the chain into canonical form (centre on the last site), then every bond is
+        SVD-truncated to chi values from right to left.  With the centre on site c, T_c as an
+        l x (p, n, r) matrix = U S V^dag carries the Schmidt decomposition of bond (c-1, c);
+        T_c <- V^dag[:k] and T_{c-1} <- T_{c-1} U[:, :k] S[:k] moves the centre to c-1.  Returns the
+        summed discarded weight of the sweep; the centre ends on site 0."""
+        self.move_centre(self.n - 1)
+        total = 0.0
+        for c in range(self.n - 1, 0, -1):
+            A = self.sites[c]
+            dl, _, dn, dr = A.shape
+            Um, s, Vh = np.linalg.svd(self._perturbed(A.reshape(dl, 2 * dn * dr)), full_matrices=False)
+            k, w = self._keep(s, chi)
+            self.sites[c] = Vh[:k].reshape(k, 2, dn, dr)
+            self.sites[c - 1] = np.einsum("lpnb,bx->lpnx", self.sites[c - 1], Um[:, :k] * s[:k])
+            self.centre = c - 1
+            self.discarded_chi += w
+            self.log.append(("chi", c - 1, k, len(s), w))
+            total += w
+        return total
 
     # ------------------------------------------------------------ noisy gates
     def apply_1q(self, q: int, U: np.ndarray, kraus) -> None:
@@ -272,7 +297,9 @@ def run_circuit(circuit, chi_max: int, kappa_max: int, tol: float = 1e-13, kraus
     st = MPDO(circuit.n, chi_max, kappa_max, tol, trunc_order=trunc_order)
     st.perturb = perturb
     for op in circuit.ops:
-        if op.kind == 1:
+        if op.kind == 3:
+            st.truncate_bonds(op.q)
+        elif op.kind == 1:
             st.apply_1q(op.q, op.U, kraus[op.chan])
         else:
             st.apply_2q(op.q, op.U, kraus[op.chan])

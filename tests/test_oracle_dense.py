@@ -125,3 +125,37 @@ def test_chi_application_matches_kraus_sum(seed):
         full = np.kron(np.eye(2), K @ U)
         ref += full @ rho @ full.conj().T
     assert np.allclose(out, ref, atol=1e-13)
+
+
+# ------------------------------------------------------------------ Uhlmann fidelity (Sec. IV.C)
+def _random_state(d, rank, rng):
+    G = rng.normal(size=(d, rank)) + 1j * rng.normal(size=(d, rank))
+    r = G @ G.conj().T
+    return r / np.trace(r).real
+
+
+def test_uhlmann_fidelity_closed_forms():
+    rng = np.random.default_rng(4)
+    d = 8
+    rho = _random_state(d, d, rng)
+    # identical states
+    assert abs(D.uhlmann_fidelity(rho, rho) - 1) < 1e-12
+    # a pure state against any state: <psi| sigma |psi>.  The square root of the rank-one state's
+    # rounding-level zero eigenvalues (about 1e-17) is about sqrt(u) = 1e-8, hence the tolerance
+    psi = rng.normal(size=d) + 1j * rng.normal(size=d)
+    psi /= np.linalg.norm(psi)
+    pure = np.outer(psi, psi.conj())
+    assert abs(D.uhlmann_fidelity(pure, rho) - (psi.conj() @ rho @ psi).real) < 1e-7
+    # commuting (diagonal) states: the classical fidelity (sum sqrt(p q))^2
+    p, q = rng.dirichlet(np.ones(d)), rng.dirichlet(np.ones(d))
+    assert abs(D.uhlmann_fidelity(np.diag(p), np.diag(q)) - np.sum(np.sqrt(p * q)) ** 2) < 1e-12
+    # against the maximally mixed state: (sum sqrt(lambda))^2 / d
+    lam = np.linalg.eigvalsh(rho)
+    assert abs(D.uhlmann_fidelity(rho, np.eye(d) / d) - np.sum(np.sqrt(np.clip(lam, 0, None))) ** 2 / d) < 1e-12
+    # symmetric, unitarily invariant, in [0, 1], scale-free
+    sig = _random_state(d, d, rng)
+    U = W.random_unitary(d, rng)
+    f = D.uhlmann_fidelity(rho, sig)
+    assert abs(f - D.uhlmann_fidelity(sig, rho)) < 1e-10
+    assert abs(f - D.uhlmann_fidelity(U @ rho @ U.conj().T, U @ sig @ U.conj().T)) < 1e-10
+    assert 0 <= f <= 1 and abs(f - D.uhlmann_fidelity(3 * rho, 0.5 * sig)) < 1e-12

@@ -230,3 +230,74 @@ def test_kraus_first_under_truncation_is_a_valid_state_close_to_split_first():
     assert eb < 10 * ea + 1e-3 and ea < 10 * eb + 1e-3
     # every kappa cut of kraus_first happens inside the two-qubit update (no separate truncation of q+1)
     assert sum(1 for e in b.log if e[0] == "kappa") == sum(1 for e in a.log if e[0] == "kappa")
+
+
+# ------------------------------------------------------------------ global bond truncation (Sec. II.D, Fig. 3b)
+def _purified(sites):
+    """psi[(p_0, n_0), (p_1, n_1), ...] contracted from the site tensors by plain einsums."""
+    psi = np.ones((1, 1), dtype=np.complex128)  # [left block, bond]
+    for A in sites:
+        dl, _, dn, dr = A.shape
+        psi = np.einsum("xl,lpnr->xpnr", psi, A).reshape(-1, dr)
+    return psi[:, 0]
+
+
+def _rho_of_purified(psi, n, dns):
+    """rho = sum over every Kraus index of psi psi^dag, psi indexed [(p_0, n_0), ..., (p_{n-1}, n_{n-1})]."""
+    T = psi.reshape([x for dn in dns for x in (2, dn)])
+    phys = list(range(0, 2 * n, 2))
+    kr = list(range(1, 2 * n, 2))
+    T = T.transpose(phys + kr).reshape(2 ** n, -1)
+    return T @ T.conj().T
+
+
+def _noisy_state(n, seed, rank1=3, rank2=6, ops=14):
+    rng = np.random.default_rng(seed)
+    circ = W.random_circuit(n, ops, rng, rank1=rank1, rank2=rank2)
+    return M.run_circuit(circ, 4096, 4096), circ
+
+
+def test_global_bond_truncation_exact_when_chi_covers_ranks():
+    st, circ = _noisy_state(4, 40)
+    rho = st.dense()
+    w = st.truncate_bonds(max(st.bond_dims()))
+    assert w < 1e-24
+    assert st.centre == 0
+    assert np.max(np.abs(st.dense() - rho)) < 1e-12
+    assert np.max(np.abs(rho - D.run_circuit(circ))) < 1e-12
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_global_bond_truncation_is_sequential_eckart_young(seed):
+    """The sweep keeps, at every cut from the right end to the left, the best rank-chi approximation
+    of the purified state across that cut (Eckart-Young applied to the whole state vector, cut by
+    cut, in the sweep's order); its discarded weights are those of the dropped Schmidt values."""
+    n = 4
+    st, _ = _noisy_state(n, 50 + seed)
+    dns = st.kraus_dims()
+    psi = _purified(st.sites)
+    chi = 2
+    ref_w = []
+    for c in range(n - 1, 0, -1):
+        left = int(np.prod([2 * d for d in dns[:c]]))
+        Psi = psi.reshape(left, -1)
+        Um, s, Vh = np.linalg.svd(Psi, full_matrices=False)
+        nz = int(np.sum(s > 1e-13 * s[0]))
+        k = min(chi, nz)
+        ref_w.append(float(np.sum(s[k:] ** 2) / np.sum(s ** 2)))
+        psi = ((Um[:, :k] * s[:k]) @ Vh[:k]).reshape(-1)
+    assert max(ref_w) > 1e-4
+    st.truncate_bonds(chi)
+    got_w = [e[4] for e in st.log if e[0] == "chi"][-(n - 1):]
+    assert np.allclose(got_w, ref_w, atol=1e-12)
+    assert max(st.bond_dims()) <= chi
+    assert np.max(np.abs(st.dense() - _rho_of_purified(psi, n, dns))) < 1e-12
+
+
+def test_global_bond_truncation_leaves_right_isometries():
+    st, _ = _noisy_state(5, 60)
+    st.truncate_bonds(3)
+    for c in range(1, st.n):
+        A = st.sites[c]
+        Am = A.reshape(A.shape[0], -1)
+        assert np.max(np.abs(Am @ Am.conj().T - np.eye(A.shape[0]))) < 1e-12
