@@ -5,7 +5,10 @@ unit roundoff of the eigensolvers).
 
 * Readouts (normalised expectations, density-matrix entries, probabilities): the bound the target
   states per result, 1e-6 absolute in MIXED (complex64 contractions, FP64 truncation eigensolvers)
-  and 1e-10 in FP64.  FP32 mode (complex64 with FP32 eigensolvers) is not one of the target's
+  and 1e-10 in FP64, on the readouts of the unnormalised state Tr(rho O), whose norm starts at 1.
+  Every rounding error is committed relative to the norm of the state at that time, and nothing is
+  renormalised (Sec. II.D truncations only discard weight, the channels preserve the trace), so on
+  a normalised readout Tr(rho O) / Tr(rho) the bound becomes bound / Tr(rho) of the final state.  FP32 mode (complex64 with FP32 eigensolvers) is not one of the target's
   modes: its eigensolvers add a backward error of about sqrt(n) u32 ||G|| per truncation, up to
   sqrt(256) = 16 times the complex64 Gram's own 2 u32, so its readouts are held to 3e-6.  The only
   addition is the oracle's cut_allowance(threshold): truncations whose relative eigenvalue gap at
@@ -35,8 +38,8 @@ def allowance(orc, prec: str) -> float:
 
 
 def readout_limit(orc, prec: str, scale: float = 1.0) -> float:
-    """Bound on |GPU - oracle| for a readout of an operator of norm `scale`."""
-    return scale * (MODES[prec][0] + allowance(orc, prec))
+    """Bound on |GPU - oracle| for a normalised readout of an operator of norm `scale`."""
+    return scale * (MODES[prec][0] / min(1.0, orc.trace()) + allowance(orc, prec))
 
 
 def discarded_limit(orc, prec: str, kind: str) -> float:
