@@ -48,6 +48,23 @@ __host__ __device__ __forceinline__ void cfma_cj(cplx<R>& acc, cplx<R> a, cplx<R
   acc.y = fma(-a.y, b.x, acc.y);
 }
 
+// acc -= a * b and acc -= a * conj(b), four fused multiply-adds each (the operator form costs two
+// multiplications, two fused multiply-adds and two additions)
+template <typename R>
+__host__ __device__ __forceinline__ void cfms(cplx<R>& acc, cplx<R> a, cplx<R> b) {
+  acc.x = fma(-a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(-a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+}
+template <typename R>
+__host__ __device__ __forceinline__ void cfms_cj(cplx<R>& acc, cplx<R> a, cplx<R> b) {
+  acc.x = fma(-a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(-a.y, b.x, acc.y);
+  acc.y = fma(a.x, b.y, acc.y);
+}
+
 // Norms below this are treated as exact zeros by the Householder steps, so that 1 / (|x| (|x| + |a|))
 // cannot overflow (its square stays far above the smallest normal number).
 template <typename R>

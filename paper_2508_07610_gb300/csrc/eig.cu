@@ -18,10 +18,11 @@
 //
 // FP64 on this GPU has 1/64 of the FP32 issue rate, so the FP64 instantiation saves FP64 operations
 // where it can without losing accuracy: the reduction updates only the lower triangle of the
-// trailing block, the off-diagonal magnitudes are taken once, and the substitutions of the inverse
-// iteration multiply by reciprocal pivots instead of dividing.  (Shifts from an FP32 bisection were
-// tried and rejected: they cannot separate eigenvalues closer than about u32 ||T||, and cuts with
-// relative gaps between 1e-9 and 1e-6 then lost FP64 accuracy.)
+// trailing block with fused complex multiply-adds, the off-diagonal magnitudes are taken once, the
+// substitutions of the inverse iteration multiply by reciprocal pivots instead of dividing, and the
+// bisection starts from an FP32 bracket confirmed by FP64 Sturm counts.  (Taking the FP32 values as
+// the final shifts was tried and rejected: they cannot separate eigenvalues closer than about
+// u32 ||T||, and cuts with relative gaps between 1e-9 and 1e-6 then lost FP64 accuracy.)
 #include "device_once.cuh"
 #include "kernels.h"
 #include "panel.cuh"
@@ -92,9 +93,10 @@ __device__ int sturm_count(const R* d, const R* e2, int n, R sigma, R pivmin) {
 }
 
 template <typename R, int NB>
-__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) heevk_kernel(EigArgs<R> g) {
+__global__ void __launch_bounds__(NT, 2) heevk_kernel(EigArgs<R> g) {
   __shared__ R red[NT / 32];
   __shared__ R s_d[MAXN], s_e2[MAXN], s_beta[MAXN], s_eabs[MAXN];
+  __shared__ float s_d32[sizeof(R) == 8 ? MAXN : 1], s_e232[sizeof(R) == 8 ? MAXN : 1];
   __shared__ cplx<R> s_p[MAXN], s_v[MAXN];
   __shared__ R s_w[MAXN];
   __shared__ cplx<R> s_v0[MAXN];
@@ -133,8 +135,8 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) heevk_kernel(EigAr
       for (int i = j + tid; i < n; i += NT) {
         cplx<R> c = col[i];
         for (int l = 0; l < jj; ++l) {
-          c = c - Vb[l * n + i] * conjg(Wb[l * n + j]);
-          c = c - Wb[l * n + i] * conjg(Vb[l * n + j]);
+          cfms_cj(c, Vb[l * n + i], Wb[l * n + j]);
+          cfms_cj(c, Wb[l * n + i], Vb[l * n + j]);
         }
         col[i] = c;
       }
@@ -202,8 +204,8 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) heevk_kernel(EigAr
           for (int i = j + 1 + tid; i < n; i += NT) {
             cplx<R> acc = s_p[i];
             for (int l = 0; l < jj; ++l) {
-              acc = acc - Vb[l * n + i] * s_x[l];
-              acc = acc - Wb[l * n + i] * s_x[jj + l];
+              cfms(acc, Vb[l * n + i], s_x[l]);
+              cfms(acc, Wb[l * n + i], s_x[jj + l]);
             }
             s_p[i] = beta * acc;
           }
@@ -211,7 +213,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) heevk_kernel(EigAr
         for (int i = j + 1 + tid; i < n; i += NT) {
           // the column loads of a block of MV columns are all issued before any is used, so a
           // thread has MV L2 requests in flight instead of one
-          constexpr int MV = 16;
+          constexpr int MV = sizeof(R) == 8 ? 8 : 16;
           cplx<R> acc0 = mk<R>(0, 0), acc1 = mk<R>(0, 0), acc2 = mk<R>(0, 0), acc3 = mk<R>(0, 0);
           int c = j + 1;
           for (; c + MV <= n; c += MV) {
@@ -229,8 +231,8 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) heevk_kernel(EigAr
           for (; c < n; ++c) cfma(acc0, A[(int64_t)c * n + i], s_v[c]);
           cplx<R> acc = (acc0 + acc1) + (acc2 + acc3);
           for (int l = 0; l < jj; ++l) {
-            acc = acc - Vb[l * n + i] * s_x[l];
-            acc = acc - Wb[l * n + i] * s_x[jj + l];
+            cfms(acc, Vb[l * n + i], s_x[l]);
+            cfms(acc, Wb[l * n + i], s_x[jj + l]);
           }
           s_p[i] = beta * acc;
         }
@@ -272,8 +274,8 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) heevk_kernel(EigAr
         if (kLowerOnly<R>() && i < c) continue;  // the upper triangle is never read again
         cplx<R> w = v[u];
         for (int l = 0; l < pb; ++l) {
-          w = w - Vb[l * n + i] * conjg(Wb[l * n + c]);
-          w = w - Wb[l * n + i] * conjg(Vb[l * n + c]);
+          cfms_cj(w, Vb[l * n + i], Wb[l * n + c]);
+          cfms_cj(w, Wb[l * n + i], Vb[l * n + c]);
         }
         A[(int64_t)c * n + i] = w;
       }
@@ -315,9 +317,36 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) heevk_kernel(EigAr
   gl -= R(2) * eps * tnorm * n + pivmin;
   gu += R(2) * eps * tnorm * n + pivmin;
   for (int i = tid; i < n; i += NT) s_eabs[i] = (i + 1 < n) ? sqrt(s_e2[i]) : R(0);
+  if constexpr (sizeof(R) == 8) {
+    for (int i = tid; i < n; i += NT) {
+      s_d32[i] = (float)s_d[i];
+      s_e232[i] = (float)s_e2[i];
+    }
+    __syncthreads();
+  }
   for (int t = tid; t < kk; t += NT) {
     const int target = n - 1 - t;  // ascending index of the t-th largest eigenvalue
     R lo = gl, hi = gu;
+    if constexpr (sizeof(R) == 8) {
+      // FP64 Sturm counts divide on a pipe 64 times narrower than FP32: bracket the eigenvalue in
+      // FP32 first, widen the bracket by the FP32 counts' error, keep it if two FP64 counts confirm
+      // it, and let the FP64 bisection below finish from there (same result, fewer FP64 counts)
+      const float e32 = eps_of<float>(), tn32 = (float)tnorm;
+      const float piv32 = fmaxf(1e-30f * fmaxf(1.f, (float)emax2), 1e-36f);
+      float l32 = (float)gl, h32 = (float)gu;
+      for (int it = 0; it < 128; ++it) {
+        const float mid = 0.5f * (l32 + h32);
+        if (h32 - l32 <= 2.f * e32 * fmaxf(fabsf(l32), fabsf(h32)) + e32 * tn32 + piv32 || mid == l32 || mid == h32)
+          break;
+        if (sturm_count(s_d32, s_e232, n, mid, piv32) > target) h32 = mid; else l32 = mid;
+      }
+      const R pad = R(16) * R(e32) * tnorm + pivmin;
+      const R blo = R(l32) - pad, bhi = R(h32) + pad;
+      if (sturm_count(s_d, s_e2, n, blo, pivmin) <= target && sturm_count(s_d, s_e2, n, bhi, pivmin) > target) {
+        lo = blo;
+        hi = bhi;
+      }
+    }
     for (int it = 0; it < 256; ++it) {
       R mid = R(0.5) * (lo + hi);
       if (hi - lo <= R(2) * eps * fmax(fabs(lo), fabs(hi)) + abstol || mid == lo || mid == hi) break;
@@ -656,7 +685,9 @@ template <typename R>
 cudaError_t heevk(cudaStream_t s, int batch, const EigArgs<R>& g) {
   if (batch <= 0 || g.n <= 0 || g.k <= 0) return cudaSuccess;
   if (g.n > MAXN || g.k > g.n || g.k + 1 > MAXN / 2) return cudaErrorInvalidValue;
-  constexpr int NB = 8;  // reflectors per panel (tridiagonalisation and back-transformation)
+  // reflectors per panel (tridiagonalisation and back-transformation); FP64 takes 4 so that two
+  // matrices share an SM and fill each other's barrier waits on the narrow FP64 pipe
+  constexpr int NB = sizeof(R) == 8 ? 4 : 8;
   const size_t bytes = 2 * sizeof(cplx<R>) * (size_t)NB * g.n + sizeof(R) * (size_t)GB * g.k;
   static PerDevice setup;
   static size_t dyn_max[kMaxDevices];
