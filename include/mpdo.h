@@ -34,6 +34,7 @@ extern "C" {
 typedef struct mpdo_ctx* mpdo_t;
 typedef struct mpdo_chanset* mpdo_chan_t;
 typedef struct mpdo_graph* mpdo_graph_t;
+typedef struct mpdo_batch* mpdo_batch_t;
 
 typedef enum {
   MPDO_OK = 0,
@@ -41,8 +42,9 @@ typedef enum {
   MPDO_ENOMEM = 2,   /* device or host allocation failed */
   MPDO_ENOTCP = 3,   /* process matrix is not completely positive (negative Choi mass > 1e-8) */
   MPDO_ENOTTP = 4,   /* process matrix is not trace preserving (|Tr chi - 1| > 1e-8 or sum K^H K != I) */
-  MPDO_ENOCONV = 5,  /* a readout came out non-finite */
-  MPDO_ETIMEOUT = 6, /* reserved */
+  MPDO_ENOCONV = 5,  /* an eigensolver (truncation or chi -> Kraus) produced non-finite or collapsed
+                        eigenpairs, or a readout came out non-finite */
+  MPDO_ETIMEOUT = 6, /* a bounded wait inside a kernel (tensor-core pipelines) ran out */
   MPDO_ECUDA = 7,    /* CUDA runtime error */
   MPDO_ESTATE = 8    /* call not valid in the handle's current state (e.g. during capture) */
 } mpdo_status;
@@ -77,7 +79,10 @@ mpdo_status mpdo_init_batch(int batch, int n, int chi_max, int kappa_max, int pr
 mpdo_status mpdo_free(mpdo_t h);
 /* Back to |0..0> with zero discarded weight. Capturable. */
 mpdo_status mpdo_reset(mpdo_t h);
-/* Wait for the handle's stream. */
+/* Wait for the handle's stream.  Kernels record failures in a status word of the handle; this call
+ * and `expect` read and clear it: MPDO_ENOCONV when an eigensolver produced non-finite or collapsed
+ * eigenpairs since the last read (for example from non-finite site data), MPDO_ETIMEOUT when a
+ * kernel's bounded wait ran out (the kernel skipped its output; the handle's state is unspecified). */
 mpdo_status mpdo_sync(mpdo_t h);
 
 /* chi -> Kraus (Sec. III): Lambda = sum_mn chi_mn |s_m>><<s_n|, Lambda = sum_i eta_i |psi_i><psi_i|,
@@ -110,8 +115,24 @@ mpdo_status apply_2q_batch(mpdo_t h, int q, const double* U_dev, mpdo_chan_t ch,
 /* Truncate qubit q's Kraus leg to kappa (<= 0: kappa_max), Eq. svdNoise.  discarded (host, nullable)
  * receives batch relative discarded weights (synchronises when non-NULL). */
 mpdo_status truncate_kraus(mpdo_t h, int q, int kappa, double* discarded);
+/* Global bond truncation of Sec. II.D (Fig. 3b), the paper's own schedule: QR decompositions from
+ * left to right bring the chain into canonical form, then every bond is truncated to chi (>= 1)
+ * Schmidt values from right to left, each by the eigen-decomposition of its Gram matrix with the
+ * centre on the bond's right site.  The centre ends on site 0.  To run this schedule, create the
+ * handle with chi_max large enough that the per-gate splits keep every bond's rank, and call this
+ * after each layer of gates.  discarded (host, nullable) receives batch summed relative discarded
+ * weights of this sweep (synchronises when non-NULL).  MPDO_EINVAL for chi < 1. */
+mpdo_status truncate_bonds(mpdo_t h, int chi, double* discarded);
 /* Readouts (Sec. II.C local densities, Eqs. maxcut / maxcut_obj); out: host, see MPDO_EXPECT_*. */
 mpdo_status expect(mpdo_t h, int kind, const int* args, int nargs, double* out);
+
+/* Uhlmann fidelity F(rho, sigma) = (tr sqrt(sqrt(rho) sigma sqrt(rho)))^2 (Sec. IV.C, Eq. fidelity)
+ * between chain chain_a of a and chain chain_b of b, both normalised to unit trace; the paper uses it
+ * to compare truncated with untruncated states.  Dense and in FP64 whatever the handles' precision:
+ * each chain's 2^n x 2^n density matrix is contracted from its sites, so n <= 7 (MPDO_EINVAL
+ * otherwise, or when an intermediate of the contraction would exceed 2 GB).  Synchronises both
+ * handles, allocates its temporaries and frees them before returning; MPDO_ESTATE during capture. */
+mpdo_status mpdo_fidelity(mpdo_t a, int chain_a, mpdo_t b, int chain_b, double* out);
 
 /* Checkpoint: dims, centre, discarded weights and every site tensor of every chain (versioned). */
 mpdo_status mpdo_save(mpdo_t h, const char* path);
@@ -134,6 +155,17 @@ mpdo_status mpdo_graph_free(mpdo_graph_t g);
 mpdo_status mpdo_get_site(mpdo_t h, int chain, int q, double* out, int* dims);
 mpdo_status mpdo_set_site(mpdo_t h, int q, int dl, int dn, int dr, const double* data);
 mpdo_status mpdo_set_centre(mpdo_t h, int q);
+
+/* Order of the two truncations of a two-qubit update (Sec. II.D leaves the schedule open):
+ *   MPDO_TRUNC_SPLIT_FIRST (default): split the merged pair's bond to chi_max (Fig. 3b), then truncate
+ *     site q+1's Kraus leg, r_k kappa wide, to kappa_max (Eq. svdNoise);
+ *   MPDO_TRUNC_KRAUS_FIRST: truncate the merged tensor's new Kraus leg to kappa_max first (Eq. svdNoise
+ *     applied to the two-site tensor), then split the bond; the split sees a kappa-wide leg, which
+ *     takes about 2.4 times fewer multiply-adds at chi = 64, kappa = 8, r_k = 16.
+ * The two orders keep the same state when the bond is not cut; otherwise they are different
+ * approximations.  Read when each apply_2q call is made (capturable); MPDO_EINVAL for other values. */
+enum { MPDO_TRUNC_SPLIT_FIRST = 0, MPDO_TRUNC_KRAUS_FIRST = 1 };
+mpdo_status mpdo_set_trunc_order(mpdo_t h, int order);
 
 /* When enabled, a noisy 1q gate on a site next to the orthogonality centre truncates its Kraus leg
  * through the centre's environment (the Gram of the centre over the shared bond) instead of first
@@ -176,29 +208,80 @@ mpdo_status mpdo_profile_read(mpdo_t h, double* ms, double* flops, long long* co
  *   chi_dev   device, count x (4^nq x 4^nq) complex, row-major (same layout as the host variant)
  *   kraus_dev device output, count x 4^nq Kraus operators of 2^nq x 2^nq complex (descending weight,
  *             pruned ones zeroed: eta <= tol * max eta, tol <= 0 means 1e-12)
- *   ranks_dev device output, count ints
+ *   ranks_dev device output, count ints: the Kraus rank, or -1 when the process matrix is not
+ *             completely positive (negative Choi mass > 1e-8) and -2 when the converted set is not
+ *             trace preserving (|sum K^H K - I| > 1e-8); that channel's operators are then zero
  *   stream    cudaStream_t the work is enqueued on (returns without waiting)
- * Returns MPDO_EINVAL for nq not in {1, 2}, count < 1 or count > MPDO_NOALLOC_MAX_CHANNELS; inputs
- * are not validated (no host copy exists).  It calls no allocating routine.  The first call on a
- * device looks up the array's device address (once per device, with that device current); make
- * that first call before any stream capture.  All calls share the one array: calls whose work
+ * Returns MPDO_EINVAL for nq not in {1, 2}, count < 1 or count > MPDO_NOALLOC_MAX_CHANNELS; the
+ * inputs are checked on the device only (the sentinel ranks above; no host copy exists).  It calls
+ * no allocating routine.  The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream capture.  All calls share the one array: calls whose work
  * overlaps on the GPU (different streams, or several host threads) race; serialise them. */
 #define MPDO_NOALLOC_MAX_CHANNELS 64
 mpdo_status channel_kraus_noalloc(int nq, int count, const double* chi_dev, double tol, double* kraus_dev,
                                   int* ranks_dev, void* stream);
 
-/* In the complex64 modes, products with at least 128 rows and 64 columns, an inner dimension of at
- * most 2048 and a non-Hermitian result run on the tensor cores (tcgen05.mma, each FP32 operand split
- * into two TF32 parts, three TF32 products per real product, FP32 accumulation); the others, and
- * every product when this is off, run on the CUDA cores.  Off by default: the tensor cores' FP32
- * accumulation leaves about 2e-6 relative error on a 128-long product (the CUDA-core GEMM about 1e-7),
- * which takes a full-size two-qubit update past 1e-6.  No effect in MPDO_FP64. */
+/* In the complex64 modes (MIXED, FP32) the dense complex products with at least 128 rows, 64 columns
+ * and an inner dimension of 16 run on the tensor cores (tcgen05.mma kind::tf32): each FP32 operand is
+ * split into TF32 hi and lo parts (three real products per real product, four real products per
+ * complex product), and the tensor-memory accumulator is folded every 16 k into compensated FP32
+ * sums, so the error matches the CUDA-core GEMM's.  On by default in those modes (the handle holds
+ * workspaces for the split operands, sized at creation); 0 keeps every product on the CUDA cores.
+ * No effect in MPDO_FP64.  MPDO_ESTATE during capture when it would allocate. */
 mpdo_status mpdo_set_tensor_cores(mpdo_t h, int enable);
 
-/* Diagnostic: multiplies random complex64 M x K and K x N matrices with the tensor-core GEMM (tcgen05,
- * TF32 split into hi + lo parts, FP32 accumulation) and with the CUDA-core GEMM, and returns the
- * largest entry-wise difference relative to the largest entry, and the kernel's wait-timeout flag. */
+/* Diagnostic: multiplies random complex64 M x K and K x N matrices (M >= 128, N >= 64, K >= 16) with
+ * the tensor-core GEMM and with the CUDA-core GEMM, and returns the largest entry-wise difference
+ * relative to the largest entry, and the tensor-core kernel's status word (2 = a wait timed out). */
 mpdo_status mpdo_tc_selftest(int M, int N, int K, double* max_rel_err, int* err_flag);
+
+/* Diagnostic: one thread waits on a shared-memory mbarrier that nothing arrives on, with the same
+ * time-bounded wait the tensor-core kernels use, limited to limit_us microseconds (1 .. 1e6).  The
+ * wait gives up, the kernel records the timeout in a status word and returns: MPDO_ETIMEOUT, with
+ * the word in *status_out.  Demonstrates that no wait in the library can hang the GPU. */
+mpdo_status mpdo_wait_selftest(int limit_us, int* status_out);
+
+/* ---- Batched runtime: many independent noisy circuits ("instances") on one GPU.  The paper runs one
+ * circuit at a time; this is the throughput form of the same per-gate update (Sec. II.C-II.D).
+ * Instance c has n_qubits[c] qubits (starting in |0..0>) and the ops op_begin[c] .. op_begin[c+1]-1:
+ *   op_kind[o]  1 or 2 (the gate acts on op_q[o], or on op_q[o] and op_q[o]+1), or
+ *               MPDO_OP_TRUNCATE_BONDS: the global bond truncation truncate_bonds(h, op_q[o], NULL)
+ *               (1 <= op_q[o] <= chi_max; op_U and op_chi of the op are not read)
+ *   op_U[o]     32 doubles: the 2x2 or 4x4 gate, complex row-major (interleaved re, im), 2x2 in the
+ *               first 8 doubles
+ *   op_chi[o]   index of the channel that follows the gate in the process-matrix table chis: n_chi
+ *               matrices back to back, matrix m is 4^chi_nq[m] x 4^chi_nq[m] complex (Eq. chi), with
+ *               chi_nq[m] equal to the op's kind
+ * Instances whose gates sit on the same positions in the same order form a group; a group runs as one
+ * or more handles of batched chains, each captured into one CUDA graph on its own stream.  With a
+ * tuning file (nullable path), groups of at least 128 instances not yet in the file are timed over
+ * every schedule (1, 2 or 4 handles; tensor cores on or off in the complex64 modes) and the fastest
+ * is stored in the file as JSON; entries found in the file are used without timing.  All host arrays
+ * are copied.  MPDO_EINVAL for inconsistent arrays; the channel checks of
+ * channel_set_from_process_matrices apply (MPDO_ENOTCP, MPDO_ENOTTP). */
+enum { MPDO_OP_TRUNCATE_BONDS = 3 };
+mpdo_status mpdo_batch_create(int count, const int* n_qubits, const int* op_begin, const int* op_kind, const int* op_q,
+                              const double* op_U, const int* op_chi, int n_chi, const int* chi_nq, const double* chis,
+                              int chi_max, int kappa_max, int prec, const char* tuning_path, mpdo_batch_t* out);
+/* Replay every instance's circuit from |0..0> (asynchronous; the groups run concurrently). */
+mpdo_status mpdo_batch_run(mpdo_batch_t b);
+/* Wait for the run; the first status word error of any handle (see mpdo_sync) is returned. */
+mpdo_status mpdo_batch_sync(mpdo_batch_t b);
+/* Per-instance readouts, out in instance order: MPDO_EXPECT_TRACE, _GHZ, _PURITY (1 value each),
+ * _DISCARDED (3 each), _ZZ_MAP (n_qubits[c]^2 each, packed), _MAXCUT (1 each: instance c's edges are
+ * the pairs of chain positions args[arg_begin[c]] .. args[arg_begin[c+1]-1]).  Synchronises. */
+mpdo_status mpdo_batch_expect(mpdo_batch_t b, int kind, const int* arg_begin, const int* args, double* out);
+/* Number of groups and handles, and the two-qubit updates of one run. */
+mpdo_status mpdo_batch_info(mpdo_batch_t b, int* groups, int* handles, long long* updates_2q);
+/* Schedule of group g: its qubit count, instances, handles, tensor-core setting and the tuner's time
+ * per replay in ms (0 when not timed). */
+mpdo_status mpdo_batch_schedule(mpdo_batch_t b, int group, int* n_qubits, int* chains, int* handles,
+                                int* tensor_cores, double* tuned_ms);
+/* Uhlmann fidelity (mpdo_fidelity) of every instance of a against the same instance of b, for two
+ * batches built from the same circuits (typically different caps): count values in instance order.
+ * Call after both have run. */
+mpdo_status mpdo_batch_fidelity(mpdo_batch_t a, mpdo_batch_t b, double* out);
+mpdo_status mpdo_batch_free(mpdo_batch_t b);
 
 /* Number of kernels the library launched on this handle since creation (for accounting). */
 long long mpdo_launch_count(mpdo_t h);

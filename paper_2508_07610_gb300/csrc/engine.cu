@@ -135,6 +135,7 @@ struct EngBase {
   virtual mpdo_status apply(int nq, int q, const double* Uhost, const double* Udev, const mpdo_chanset* ch,
                             const int* idx_dev) = 0;
   virtual mpdo_status truncate(int q, int kappa, double* disc) = 0;
+  virtual mpdo_status truncate_bonds(int chi, double* disc) = 0;
   virtual mpdo_status expect(int kind, const int* args, int nargs, double* out) = 0;
   virtual mpdo_status restore_layout() = 0;
   virtual std::vector<int> slots() const = 0;
@@ -144,6 +145,9 @@ struct EngBase {
   virtual mpdo_status set_site(int q, int dl, int dn, int dr, const double* data) = 0;
   virtual mpdo_status load(FILE* f) = 0;
   virtual mpdo_status alloc_tc() = 0;
+  // dense density matrix of one chain (small n), FP64, see Eng::dense_rho
+  virtual int64_t dense_work() const = 0;
+  virtual mpdo_status dense_rho(int chain, cudaStream_t s, cplx<double>* X, cplx<double>* Y, cplx<double>* S) = 0;
 
   int* dStatus = nullptr;  // device status word: kStatusNoConv | kStatusTimeout bits set by kernels
 
@@ -292,6 +296,69 @@ struct Eng : EngBase {
     mpdo_status st = reset();
     if (st) return st;
     return sync();
+  }
+
+  // Elements of each of the two work buffers dense_rho needs: the largest intermediate of its
+  // contraction, 4^q dl (2 dn dr) at site q.
+  int64_t dense_work() const override {
+    int64_t w = 1;
+    for (int q = 0; q < n; ++q) {
+      const int64_t M2 = (int64_t)1 << (2 * q);
+      w = lmax(w, M2 * bond[q] * 2 * kraus[q] * bond[q + 1]);
+      w = lmax(w, M2 * 4 * (int64_t)bond[q + 1] * bond[q + 1]);
+    }
+    return w;
+  }
+  // rho of one chain, row-major 2^n x 2^n FP64 in X (basis index with qubit 0 most significant), by
+  // the contraction of Sec. II.C site by site: R[(A),(B), l, l'] -> R'[(A a),(B b), r, r'] =
+  // sum_{l, l', n} R[A, B, l, l'] T[l, a, n, r] conj(T[l', b, n, r']) as two products with permutes.
+  // X, Y: dense_work() elements each; S: one site in FP64 (slot_elems).
+  mpdo_status dense_rho(int chain, cudaStream_t s, cplx<double>* X, cplx<double>* Y, cplx<double>* S) override {
+    CK(fill<double>(s, 1, X, mk<double>(1, 0)));
+    for (int q = 0; q < n; ++q) {
+      const int dl = bond[q], dn = kraus[q], dr = bond[q + 1];
+      const int64_t Mq = (int64_t)1 << q, M2 = Mq * Mq, N1 = 2 * dn * dr;
+      CK((convert<R, double>(s, (int64_t)dl * N1, site_ptr(q) + (int64_t)chain * slot_elems, S)));
+      GemmArgs<double> g;
+      g.alpha = mk<double>(1, 0);
+      g.beta = mk<double>(0, 0);
+      // Y[(AB, l'), (a, n, r)] = sum_l R[AB, l, l'] S[l, (a, n, r)]
+      g.M = (int)(M2 * dl);
+      g.N = (int)N1;
+      g.K = dl;
+      g.A = X;
+      g.va = v2(0, dl, (int64_t)dl * dl, 1, 0, 0, dl);
+      g.B = S;
+      g.vb = row_major(N1, 0);
+      g.C = Y;
+      g.vc = row_major(N1, 0);
+      CK(gemm<double>(s, 1, g));
+      // X[AB][a][r][l'][n] from Y[AB][l'][a][n][r]
+      {
+        int dims[5] = {(int)M2, dl, 2, dn, dr};
+        int perm[5] = {0, 2, 4, 1, 3};
+        CK(permute<double>(s, 1, 5, dims, perm, Y, 0, X, 0));
+      }
+      // Y[(AB, a, r), (b, r')] = sum_{(l', n)} X[(AB, a, r), (l', n)] conj(S[l', b, n, r'])
+      g.M = (int)(M2 * 2 * dr);
+      g.N = 2 * dr;
+      g.K = dl * dn;
+      g.A = X;
+      g.va = row_major((int64_t)dl * dn, 0);
+      g.B = S;
+      g.vb = v2(0, dn, N1, dr, dr, (int64_t)dn * dr, 1, 1);
+      g.C = Y;
+      g.vc = row_major(2 * dr, 0);
+      CK(gemm<double>(s, 1, g));
+      // X[A][a][B][b][r][r'] from Y[A][B][a][r][b][r']
+      {
+        int dims[6] = {(int)Mq, (int)Mq, 2, dr, 2, dr};
+        int perm[6] = {0, 2, 1, 4, 3, 5};
+        CK(permute<double>(s, 1, 6, dims, perm, Y, 0, X, 0));
+      }
+      launches += 6;
+    }
+    return MPDO_OK;
   }
 
   // Plane workspaces of the tensor-core GEMM, sized for the largest operands of the update's products
@@ -610,6 +677,46 @@ struct Eng : EngBase {
     return env ? apply1_neighbour(q, ch->rpad) : apply1(q, ch->rpad);
   }
 
+  // Noisy 1q gate (Fig. 2c) and the Kraus-leg truncation of its site (Eq. svdNoise) without forming
+  // the extended site A' = (Khat (x) I) A, whose Kraus leg is r_k times wider.  The Gram of A' over
+  // (l, p', r) follows from the Gram of A over its bonds,
+  //   H[(p, n), (p'', n')] = sum_{l, r} conj(A[l, p, n, r]) Benv[l, p'', n', r],
+  // as G = sum_{p, p''} (Khat_k^H Khat_k')[p, p''] H (kraus_gram); its top-kappa eigenvectors V are
+  // folded into the gate, W = sum_k Khat_k V_k (kraus_fold), and the new site is one product
+  // A'' = W A.  Benv is A itself with the centre on q, or A through the centre's environment when q is
+  // its neighbour.  The site is read twice and only the truncated site is written.
+  mpdo_status apply1_fold(int q, int rk, const C* Benv, int64_t bstride) {
+    const int dl = bond[q], dn = kraus[q], dr = bond[q + 1];
+    const int NK = rk * dn, NH = 2 * dn;
+    const int64_t ld = (int64_t)2 * dn * dr;  // stride of l in a site
+    prof_sub = P_GEMM_GRAM;
+    mpdo_status st = gemm_(NH, NH, dl * dr, site_ptr(q), v2(slot_elems, 0, 0, dr, dr, ld, 1, 1), Benv,
+                           v2(bstride, dr, ld, 1, 0, 0, dr), wHk, row_major(NH, sHk));
+    prof_sub = -1;
+    if (st) return st;
+    prof_start(P_OTHER, 8.0 * NK * NK * 12 * B);
+    CK(kraus_gram<R>(stream, B, 2, rk, dn, wK, wHk, sHk, wF, sF));
+    prof_stop();
+    ++launches;
+    const int kap = imin(kappa_max, imin(2 * dl * dr, NK));
+    st = eig_(NK, kap, 1);
+    if (st) return st;
+    // W[(p', nu), (p, n)] = sum_k Khat_k[p', p] V[(k, n), nu]  (wHk, row-major 2 kap x 2 dn)
+    prof_start(P_OTHER, 8.0 * 4 * kap * dn * rk * B);
+    CK(kraus_fold<R>(stream, B, 2, rk, dn, kap, wK, wU, sU, NK, wHk, sHk));
+    prof_stop();
+    ++launches;
+    // A''[l][(p', nu)][r] = sum_{(p, n)} W[(p', nu), (p, n)] A[l][(p, n)][r]
+    const int so = take_slot();
+    st = gemm_(2 * kap, dl * dr, NH, wHk, row_major(NH, sHk), site_ptr(q), v2(slot_elems, 0, 0, dr, dr, ld, 1),
+               slot_ptr(so), v2(slot_elems, 0, 0, dr, dr, (int64_t)2 * kap * dr, 1));
+    if (st) return st;
+    give_slot(site_slot[q]);
+    site_slot[q] = so;
+    kraus[q] = kap;
+    return MPDO_OK;
+  }
+
   // Noisy 1q gate on a neighbour s of the centre c without moving the centre.  The Kraus-leg Gram of
   // s is its exact ancilla density: with every other site isometric, the sites beyond s contribute an
   // identity and the centre contributes its Gram over the shared bond, L (s = c + 1) or E (s = c - 1).
@@ -617,8 +724,7 @@ struct Eng : EngBase {
   mpdo_status apply1_neighbour(int q, int rk) {
     const int c = centre;
     const int dl = bond[q], dn = kraus[q], dr = bond[q + 1];
-    const int NK = rk * dn, S = 2 * dl;
-    const int64_t Lx = (int64_t)S * dr;
+    const int64_t ld = (int64_t)2 * dn * dr;
     const C* Ac = site_ptr(c);
     mpdo_status st;
     if (q == c + 1) {
@@ -627,54 +733,27 @@ struct Eng : EngBase {
       st = gemm_(dl, dl, K, Ac, v2(slot_elems, 0, 0, 1, 0, 0, dl, 1), Ac, row_major(dl, slot_elems), wE,
                  row_major(dl, sE));
       if (st) return st;
+      // Benv[l][(p n r)] = sum_l' L[l, l'] A[l'][(p n r)]
+      st = gemm_(dl, (int)ld, dl, wE, row_major(dl, sE), site_ptr(q), row_major(ld, slot_elems), wX, row_major(ld, sX));
     } else {
       // E[b, b'] = sum_(p,n,r) conj(Ac[b, (pnr)]) Ac[b', (pnr)],  b over bond c (= dr)
       const int K = 2 * kraus[c] * bond[c + 1];
       st = gemm_(dr, dr, K, Ac, v2(slot_elems, 0, 0, K, 0, 0, 1, 1), Ac, v2(slot_elems, 0, 0, 1, 0, 0, K), wE,
                  row_major(dr, sE));
       if (st) return st;
-    }
-    prof_start(P_OTHER, 8.0 * 2 * NK * S * dr * B);
-    CK(apply_1q_kraus<R>(stream, B, dl, dn, dr, rk, site_ptr(q), slot_elems, wK, wX, sX));
-    prof_stop();
-    ++launches;
-    if (q == c + 1) {
-      // Y[nk][b][(p r)] = sum_b' L[b, b'] X[nk][b'][(p r)]
-      st = gemm_(dl, (int)(NK * 2 * dr), dl, wE, row_major(dl, sE), wX, v2(sX, 0, 0, 2 * dr, 2 * dr, Lx, 1), wY,
-                 v2(sY, 0, 0, 2 * dr, 2 * dr, Lx, 1));
-    } else {
-      // Y[(nk l p)][b] = sum_b' X[(nk l p)][b'] E[b, b']
-      st = gemm_(NK * S, dr, dr, wX, row_major(dr, sX), wE, v2(sE, 0, 0, 1, 0, 0, dr), wY, row_major(dr, sY));
+      // Benv[(l p n)][b] = sum_b' A[(l p n)][b'] E[b, b']
+      st = gemm_(dl * 2 * dn, dr, dr, site_ptr(q), row_major(dr, slot_elems), wE, v2(sE, 0, 0, 1, 0, 0, dr), wX,
+                 row_major(dr, sX));
     }
     if (st) return st;
-    const int kap = imin(kappa_max, imin((int)Lx, NK));
-    const int so = take_slot();
-    st = kappa_truncate_X(NK, S, dr, kap, so, wY);
+    st = apply1_fold(q, rk, wX, sX);
     if (st) return st;
-    give_slot(site_slot[q]);
-    site_slot[q] = so;
-    kraus[q] = kap;
     dirty = q;
     return MPDO_OK;
   }
   int* iota = nullptr;  // device [0, 1, ..., B-1]
 
-  mpdo_status apply1(int q, int rk) {
-    const int dl = bond[q], dn = kraus[q], dr = bond[q + 1];
-    const int NK = rk * dn, S = 2 * dl;
-    prof_start(P_OTHER, 8.0 * 2 * NK * S * dr * B);
-    CK(apply_1q_kraus<R>(stream, B, dl, dn, dr, rk, site_ptr(q), slot_elems, wK, wX, sX));
-    prof_stop();
-    ++launches;
-    const int kap = imin(kappa_max, imin(S * dr, NK));
-    const int so = take_slot();
-    mpdo_status st = kappa_truncate_X(NK, S, dr, kap, so);
-    if (st) return st;
-    give_slot(site_slot[q]);
-    site_slot[q] = so;
-    kraus[q] = kap;
-    return MPDO_OK;
-  }
+  mpdo_status apply1(int q, int rk) { return apply1_fold(q, rk, site_ptr(q), slot_elems); }
 
   mpdo_status apply2(int q, int rk) {
     const int dl = bond[q], dm = bond[q + 1], dr = bond[q + 2];
@@ -809,7 +888,7 @@ struct Eng : EngBase {
     // 4. the Kraus-leg Gram G (rk dn2 square, column-major, wF) and its top-kappa eigenpairs
     const int NK = rk * dn2;
     prof_start(P_OTHER, 8.0 * NK * NK * 80 * B);
-    CK(kraus_gram<R>(stream, B, rk, dn2, wK, wHk, sHk, wF, sF));
+    CK(kraus_gram<R>(stream, B, 4, rk, dn2, wK, wHk, sHk, wF, sF));
     prof_stop();
     ++launches;
     const int kap = imin(kappa_max, imin(NK, x * 4 * dr));
@@ -817,7 +896,7 @@ struct Eng : EngBase {
     if (st) return st;
     // 5. W[(p', nu), (p, n2)] = sum_k Khat_k[p', p] V[(k, n2), nu]  (wHk, row-major 4 kap x 4 dn2)
     prof_start(P_OTHER, 8.0 * 16 * kap * dn2 * rk * B);
-    CK(kraus_fold<R>(stream, B, rk, dn2, kap, wK, wU, sU, NK, wHk, sHk));
+    CK(kraus_fold<R>(stream, B, 4, rk, dn2, kap, wK, wU, sU, NK, wHk, sHk));
     prof_stop();
     ++launches;
     // 6. Theta'[x][(p1', p2')][nu][r] = sum_{(p, n2)} W[(p', nu), (p, n2)] Theta0[x][(p, n2)][r]  (wY)
@@ -884,6 +963,66 @@ struct Eng : EngBase {
       CK(cudaMemcpyAsync(after.data(), dDisc, sizeof(double) * 3 * B, cudaMemcpyDeviceToHost, stream));
       CK(cudaStreamSynchronize(stream));
       for (int b = 0; b < B; ++b) disc[b] = after[3 * b + 1] - before[3 * b + 1];
+    }
+    return MPDO_OK;
+  }
+
+  // Global bond truncation of Sec. II.D (Fig. 3b): the centre is moved to the last site by QR
+  // decompositions from left to right (canonical form), then each bond (c-1, c) is truncated to chi
+  // from right to left.  With the centre on c, the Gram G = T_c T_c^H over the left bond (T_c as an
+  // l x (p, n, r) matrix) has the squared Schmidt values of the bond as eigenvalues; with U its top
+  // chi eigenvectors, T_c <- U^H T_c and T_{c-1} <- T_{c-1} U project the bond onto the kept
+  // Schmidt directions, and an LQ step moves the centre on to c-1.  The centre ends on site 0.
+  mpdo_status truncate_bonds(int chi, double* disc) override {
+    if (chi < 1) return MPDO_EINVAL;
+    std::vector<double> before;
+    if (disc) {
+      before.resize(3 * (size_t)B);
+      CK(cudaMemcpyAsync(before.data(), dDisc, sizeof(double) * 3 * B, cudaMemcpyDeviceToHost, stream));
+    }
+    mpdo_status st = move_centre(n - 1);
+    if (st) return st;
+    for (int c = n - 1; c >= 1; --c) {
+      const int dl = bond[c], dn = kraus[c], dr = bond[c + 1];
+      const int L = 2 * dn * dr;
+      const int k = imin(chi, imin(dl, L));
+      if (k < dl) {
+        // G[l, l'] = sum_j T_c[l, j] conj(T_c[l', j]), column-major Hermitian (wF)
+        st = gemm_(dl, dl, L, site_ptr(c), row_major(L, slot_elems), site_ptr(c), v2(slot_elems, 0, 0, 1, 0, 0, L, 1),
+                   wF, col_major(dl, sF), -1, 1);
+        if (st) return st;
+        prof_start(P_OTHER, 0);
+        CK(herm_fill_upper<R>(stream, B, dl, wF, sF));
+        prof_stop();
+        ++launches;
+        st = eig_(dl, k, 0);
+        if (st) return st;
+        // T_c' [i][j] = sum_l conj(U[l, i]) T_c[l][j]
+        const int sa = take_slot();
+        st = gemm_(k, L, dl, wU, v2(sU, 0, 0, dl, 0, 0, 1, 1), site_ptr(c), row_major(L, slot_elems), slot_ptr(sa),
+                   row_major(L, slot_elems));
+        if (st) return st;
+        // T_{c-1}' [(l, p, n)][i] = sum_b T_{c-1}[(l, p, n)][b] U[b, i]
+        const int M = bond[c - 1] * 2 * kraus[c - 1];
+        const int sb = take_slot();
+        st = gemm_(M, k, dl, site_ptr(c - 1), row_major(dl, slot_elems), wU, col_major(dl, sU), slot_ptr(sb),
+                   row_major(k, slot_elems));
+        if (st) return st;
+        give_slot(site_slot[c]);
+        give_slot(site_slot[c - 1]);
+        site_slot[c] = sa;
+        site_slot[c - 1] = sb;
+        bond[c] = k;
+      }
+      st = shift_left(c);
+      if (st) return st;
+      centre = c - 1;
+    }
+    if (disc) {
+      std::vector<double> after(3 * (size_t)B);
+      CK(cudaMemcpyAsync(after.data(), dDisc, sizeof(double) * 3 * B, cudaMemcpyDeviceToHost, stream));
+      CK(cudaStreamSynchronize(stream));
+      for (int b = 0; b < B; ++b) disc[b] = after[3 * b] - before[3 * b];
     }
     return MPDO_OK;
   }
@@ -1600,6 +1739,11 @@ mpdo_status truncate_kraus(mpdo_t h, int q, int kappa, double* discarded) {
   if (discarded && h->e->capturing) return MPDO_ESTATE;
   return h->e->truncate(q, kappa, discarded);
 }
+mpdo_status truncate_bonds(mpdo_t h, int chi, double* discarded) {
+  if (!h) return MPDO_EINVAL;
+  if (discarded && h->e->capturing) return MPDO_ESTATE;
+  return h->e->truncate_bonds(chi, discarded);
+}
 mpdo_status expect(mpdo_t h, int kind, const int* args, int nargs, double* out) {
   if (!h || !out) return MPDO_EINVAL;
   return h->e->expect(kind, args, nargs, out);
@@ -1753,6 +1897,114 @@ mpdo_status mpdo_set_tensor_cores(mpdo_t h, int enable) {
     if (st) return st;
   }
   h->e->tensor_cores = enable != 0;
+  return MPDO_OK;
+}
+
+// Uhlmann fidelity F(rho, sigma) = (tr sqrt(sqrt(rho) sigma sqrt(rho)))^2 of chain ca of a and chain cb
+// of b (Sec. IV.C), both normalised to unit trace, in FP64 on a's stream.  Each chain's dense density
+// matrix comes from its sites by the contraction of Sec. II.C (stored row-major, i.e. its complex
+// conjugate read column-major, which leaves F unchanged); sqrt(rho) = Y Y^H with Y = V diag(lambda^1/4)
+// from rho's eigendecomposition; F = (sum sqrt(mu))^2 / (tr rho tr sigma) over the eigenvalues mu of
+// sqrt(rho) sigma sqrt(rho).
+mpdo_status mpdo_fidelity(mpdo_t a, int ca, mpdo_t b, int cb, double* out) {
+  if (!a || !b || !out) return MPDO_EINVAL;
+  EngBase *ea = a->e, *eb = b->e;
+  if (ea->capturing || eb->capturing) return MPDO_ESTATE;
+  if (ea->n != eb->n || ea->n > 7 || ca < 0 || ca >= ea->B || cb < 0 || cb >= eb->B) return MPDO_EINVAL;
+  mpdo_status st = ea->clean();
+  if (!st) st = eb->clean();
+  if (!st) st = ea->sync();
+  if (!st) st = eb->sync();
+  if (st) return st;
+  const int N = 1 << ea->n;
+  const int64_t work = lmax(lmax(ea->dense_work(), eb->dense_work()), (int64_t)N * N);
+  if (work > ((int64_t)1 << 27)) return MPDO_EINVAL;  // intermediates of at most 2 GB each
+  const int64_t site = lmax(2LL * ea->kappa_max * ea->chi_max * ea->chi_max, 2LL * eb->kappa_max * eb->chi_max * eb->chi_max);
+  cudaStream_t s = ea->stream;
+  cplx<double>*X = nullptr, *Y = nullptr, *S = nullptr, *rho = nullptr, *sig = nullptr, *V = nullptr, *T1 = nullptr,
+               *T2 = nullptr;
+  double *w = nullptr, *scr = nullptr;
+  const int64_t NN = (int64_t)N * N, sc = eig_scratch_elems(N, N);
+  auto ok = [](cudaError_t e) { return e == cudaSuccess; };
+  bool good = ok(cudaMalloc((void**)&X, sizeof(cplx<double>) * work)) &&
+              ok(cudaMalloc((void**)&Y, sizeof(cplx<double>) * work)) && ok(cudaMalloc((void**)&S, sizeof(cplx<double>) * site)) &&
+              ok(cudaMalloc((void**)&rho, sizeof(cplx<double>) * NN)) && ok(cudaMalloc((void**)&sig, sizeof(cplx<double>) * NN)) &&
+              ok(cudaMalloc((void**)&V, sizeof(cplx<double>) * NN)) && ok(cudaMalloc((void**)&T1, sizeof(cplx<double>) * NN)) &&
+              ok(cudaMalloc((void**)&T2, sizeof(cplx<double>) * NN)) && ok(cudaMalloc((void**)&w, sizeof(double) * N)) &&
+              ok(cudaMalloc((void**)&scr, sizeof(double) * sc));
+  st = good ? MPDO_OK : MPDO_ENOMEM;
+  auto gemm64 = [&](int M, int Nn, int K, const cplx<double>* A, View va, const cplx<double>* Bm, View vb, cplx<double>* C,
+                    View vc) {
+    GemmArgs<double> g;
+    g.M = M;
+    g.N = Nn;
+    g.K = K;
+    g.alpha = mk<double>(1, 0);
+    g.beta = mk<double>(0, 0);
+    g.A = A;
+    g.va = va;
+    g.B = Bm;
+    g.vb = vb;
+    g.C = C;
+    g.vc = vc;
+    return gemm<double>(s, 1, g) == cudaSuccess ? MPDO_OK : MPDO_ECUDA;
+  };
+  auto eig = [&](cplx<double>* A) {
+    EigArgs<double> e;
+    e.A = A;
+    e.astride = NN;
+    e.n = N;
+    e.k = N;
+    e.w = w;
+    e.wstride = N;
+    e.V = V;
+    e.vv = col_major(N, NN);
+    e.scratch = scr;
+    e.sstride = sc;
+    e.disc = nullptr;
+    e.gap = nullptr;
+    e.disc_stride = 0;
+    return heevk<double>(s, 1, e) == cudaSuccess ? MPDO_OK : MPDO_ECUDA;
+  };
+  std::vector<double> hw(N), hs(N), hmu(N);
+  std::vector<cplx<double>> hsig((size_t)NN);
+  if (!st) st = ea->dense_rho(ca, s, X, Y, S);
+  if (!st && cudaMemcpyAsync(rho, X, sizeof(cplx<double>) * NN, cudaMemcpyDeviceToDevice, s) != cudaSuccess) st = MPDO_ECUDA;
+  if (!st) st = eb->dense_rho(cb, s, X, Y, S);
+  if (!st && cudaMemcpyAsync(sig, X, sizeof(cplx<double>) * NN, cudaMemcpyDeviceToDevice, s) != cudaSuccess) st = MPDO_ECUDA;
+  if (!st && cudaMemcpyAsync(hsig.data(), sig, sizeof(cplx<double>) * NN, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    st = MPDO_ECUDA;
+  // Y = V diag(lambda^1/4), sqrt(rho) = Y Y^H
+  if (!st) st = eig(rho);
+  if (!st && (cudaMemcpyAsync(hw.data(), w, sizeof(double) * N, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+              cudaStreamSynchronize(s) != cudaSuccess))
+    st = MPDO_ECUDA;
+  double tr_rho = 0, tr_sig = 0;
+  if (!st) {
+    for (int i = 0; i < N; ++i) {
+      tr_rho += hw[i];
+      tr_sig += hsig[(size_t)i * N + i].x;
+      hs[i] = std::sqrt(std::sqrt(hw[i] > 0 ? hw[i] : 0.0));
+    }
+    if (cudaMemcpyAsync(w, hs.data(), sizeof(double) * N, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        scale_cols(s, N, V, w) != cudaSuccess)
+      st = MPDO_ECUDA;
+  }
+  if (!st) st = gemm64(N, N, N, V, col_major(N, 0), V, v2(0, 0, 0, N, 0, 0, 1, 1), T1, col_major(N, 0));  // sqrt(rho)
+  if (!st) st = gemm64(N, N, N, T1, col_major(N, 0), sig, col_major(N, 0), T2, col_major(N, 0));
+  if (!st) st = gemm64(N, N, N, T2, col_major(N, 0), T1, col_major(N, 0), rho, col_major(N, 0));
+  if (!st) st = eig(rho);
+  if (!st && (cudaMemcpyAsync(hmu.data(), w, sizeof(double) * N, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+              cudaStreamSynchronize(s) != cudaSuccess))
+    st = MPDO_ECUDA;
+  for (void* p : {(void*)X, (void*)Y, (void*)S, (void*)rho, (void*)sig, (void*)V, (void*)T1, (void*)T2, (void*)w, (void*)scr})
+    if (p) cudaFree(p);
+  if (st) return st;
+  double f = 0;
+  for (int i = 0; i < N; ++i) f += std::sqrt(hmu[i] > 0 ? hmu[i] : 0.0);
+  f = f * f / (tr_rho * tr_sig);
+  if (!std::isfinite(f)) return MPDO_ENOCONV;
+  *out = f;
   return MPDO_OK;
 }
 

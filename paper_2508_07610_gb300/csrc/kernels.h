@@ -103,11 +103,6 @@ struct FuseArgs {
 template <typename R>
 cudaError_t fuse_gate(cudaStream_t s, int batch, const FuseArgs<R>& a);
 
-// X[(k, n)][(l, p')][r] = sum_p Khat_k[p', p] A[l, p, n, r]
-template <typename R>
-cudaError_t apply_1q_kraus(cudaStream_t s, int batch, int dl, int dn, int dr, int rk, const cplx<R>* A,
-                           int64_t astride, const cplx<R>* Khat, cplx<R>* X, int64_t xstride);
-
 // T[c][a][c'][b] = sum_{p2, q2} Rt[(a,b),(p1,p2),(q1,q2)] E[(bb,p2),(bb',q2)], c = p1*dm + bb
 template <typename R>
 cudaError_t build_T(cudaStream_t s, int batch, int dm, const cplx<R>* Rt, const cplx<R>* E, int64_t estride,
@@ -117,16 +112,21 @@ template <typename R>
 cudaError_t build_Y(cudaStream_t s, int batch, int kchi, int dm, int rk, const cplx<R>* Khat, const cplx<R>* H,
                     int64_t hstride, cplx<R>* Y, int64_t ystride);
 
-// Kraus-first two-qubit update: the Kraus-leg Gram of Theta = (Khat (x) I) Theta0 from the Gram H of
-// Theta0, G[(k, n), (k', n')] = sum_{p, p''} (Khat_k^H Khat_k')[p, p''] H[(p, n), (p'', n')]
-// (G column-major rk dn square, H row-major 4 dn square), and the kept directions V (column-major,
-// ld vld) folded into the gate, W[(p', nu), (p, n)] = sum_k Khat_k[p', p] V[(k, n), nu] (row-major).
+// A new Kraus leg without forming the extended tensor (one-qubit gates, and the Kraus-first
+// two-qubit update): the Kraus-leg Gram of X = (Khat (x) I) A from the Gram H of A over its bond
+// indices, G[(k, n), (k', n')] = sum_{p, p''} (Khat_k^H Khat_k')[p, p''] H[(p, n), (p'', n')]
+// (G column-major rk dn square, H row-major d dn square, d = 2 or 4 the gate dimension), and the kept
+// directions V (column-major, ld vld) folded into the gate, W[(p', nu), (p, n)] = sum_k Khat_k[p', p]
+// V[(k, n), nu] (row-major d kap x d dn).
 template <typename R>
-cudaError_t kraus_gram(cudaStream_t s, int batch, int rk, int dn, const cplx<R>* Khat, const cplx<R>* H,
+cudaError_t kraus_gram(cudaStream_t s, int batch, int d, int rk, int dn, const cplx<R>* Khat, const cplx<R>* H,
                        int64_t hstride, cplx<R>* G, int64_t gstride);
 template <typename R>
-cudaError_t kraus_fold(cudaStream_t s, int batch, int rk, int dn, int kap, const cplx<R>* Khat, const cplx<R>* V,
-                       int64_t vstride, int vld, cplx<R>* W, int64_t wstride);
+cudaError_t kraus_fold(cudaStream_t s, int batch, int d, int rk, int dn, int kap, const cplx<R>* Khat,
+                       const cplx<R>* V, int64_t vstride, int vld, cplx<R>* W, int64_t wstride);
+
+// column scaling V[:, j] *= f[j] of a column-major n x n FP64 matrix
+cudaError_t scale_cols(cudaStream_t s, int n, cplx<double>* V, const double* f);
 
 // out(view) = in(view) for an M x N block, optional per-row scale by a diagonal d[row % dmod]
 template <typename R>

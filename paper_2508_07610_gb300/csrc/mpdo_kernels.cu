@@ -115,32 +115,6 @@ __global__ void fuse_kernel(FuseArgs<R> a) {
 }
 
 template <typename R>
-__global__ void apply1q_kernel(int dl, int dn, int dr, int rk, const cplx<R>* A, int64_t astride,
-                               const cplx<R>* Khat, cplx<R>* X, int64_t xstride) {
-  const int z = blockIdx.y;
-  const int64_t total = (int64_t)rk * dn * dl * 2 * dr;
-  const cplx<R>* Az = A + (int64_t)z * astride;
-  const cplx<R>* K = Khat + (int64_t)z * rk * 4;
-  cplx<R>* Xz = X + (int64_t)z * xstride;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    int r = (int)(e % dr);
-    int64_t t = e / dr;
-    int pp = (int)(t % 2);
-    t /= 2;
-    int l = (int)(t % dl);
-    t /= dl;
-    int n = (int)(t % dn);
-    int k = (int)(t / dn);
-    cplx<R> a0 = Az[(((int64_t)l * 2 + 0) * dn + n) * dr + r];
-    cplx<R> a1 = Az[(((int64_t)l * 2 + 1) * dn + n) * dr + r];
-    cplx<R> v = mk<R>(0, 0);
-    cfma(v, K[k * 4 + pp * 2 + 0], a0);
-    cfma(v, K[k * 4 + pp * 2 + 1], a1);
-    Xz[e] = v;
-  }
-}
-
-template <typename R>
 __global__ void build_T_kernel(int dm, const cplx<R>* Rt, const cplx<R>* E, int64_t estride, cplx<R>* T,
                                int64_t tstride) {
   const int z = blockIdx.y;
@@ -188,15 +162,16 @@ __global__ void build_Y_kernel(int kchi, int dm, int rk, const cplx<R>* Khat, co
   }
 }
 
-// Kraus-leg Gram of the merged two-site tensor, Theta = (Khat (x) I) Theta0, from the Gram H of Theta0
-// over (x, r):  G[(k, n), (k', n')] = sum_{p, p''} M_kk'[p, p''] H[(p, n), (p'', n')] with
-// M_kk' = Khat_k^H Khat_k' (4 x 4); G column-major (ld rk dn), H row-major (4 dn x 4 dn).
+// Kraus-leg Gram of a site (or merged pair) with a new Kraus leg, X = (Khat (x) I) A, from the Gram H
+// of A over its bond indices:  G[(k, n), (k', n')] = sum_{p, p''} M_kk'[p, p''] H[(p, n), (p'', n')]
+// with M_kk' = Khat_k^H Khat_k' (d x d, d = 2 for one qubit, 4 for a pair); G column-major (ld rk dn),
+// H row-major (d dn x d dn).
 template <typename R>
-__global__ void kraus_gram_kernel(int rk, int dn, const cplx<R>* Khat, const cplx<R>* H, int64_t hstride,
+__global__ void kraus_gram_kernel(int d, int rk, int dn, const cplx<R>* Khat, const cplx<R>* H, int64_t hstride,
                                   cplx<R>* G, int64_t gstride) {
   const int z = blockIdx.y;
-  const int NK = rk * dn, NH = 4 * dn;
-  const cplx<R>* K = Khat + (int64_t)z * rk * 16;
+  const int NK = rk * dn, NH = d * dn, dd = d * d;
+  const cplx<R>* K = Khat + (int64_t)z * rk * dd;
   const cplx<R>* Hz = H + (int64_t)z * hstride;
   cplx<R>* Gz = G + (int64_t)z * gstride;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)NK * NK;
@@ -204,10 +179,10 @@ __global__ void kraus_gram_kernel(int rk, int dn, const cplx<R>* Khat, const cpl
     const int a = (int)(e % NK), b = (int)(e / NK);
     const int k = a / dn, n = a % dn, k2 = b / dn, n2 = b % dn;
     cplx<R> acc = mk<R>(0, 0);
-    for (int p = 0; p < 4; ++p)
-      for (int pp = 0; pp < 4; ++pp) {
+    for (int p = 0; p < d; ++p)
+      for (int pp = 0; pp < d; ++pp) {
         cplx<R> m = mk<R>(0, 0);
-        for (int t = 0; t < 4; ++t) cfma_cj(m, K[k * 16 + t * 4 + p], K[k2 * 16 + t * 4 + pp]);
+        for (int t = 0; t < d; ++t) cfma_cj(m, K[k * dd + t * d + p], K[k2 * dd + t * d + pp]);
         cfma(acc, m, Hz[(int64_t)(p * dn + n) * NH + pp * dn + n2]);
       }
     Gz[e] = acc;
@@ -215,21 +190,30 @@ __global__ void kraus_gram_kernel(int rk, int dn, const cplx<R>* Khat, const cpl
 }
 
 // The kept Kraus directions folded into the fused gate:
-//   W[(p', nu), (p, n)] = sum_k Khat_k[p', p] V[(k, n), nu]   (row-major 4 kap x 4 dn; V column-major, ld vld)
+//   W[(p', nu), (p, n)] = sum_k Khat_k[p', p] V[(k, n), nu]   (row-major d kap x d dn; V column-major, ld vld)
 template <typename R>
-__global__ void kraus_fold_kernel(int rk, int dn, int kap, const cplx<R>* Khat, const cplx<R>* V, int64_t vstride,
-                                  int vld, cplx<R>* W, int64_t wstride) {
+__global__ void kraus_fold_kernel(int d, int rk, int dn, int kap, const cplx<R>* Khat, const cplx<R>* V,
+                                  int64_t vstride, int vld, cplx<R>* W, int64_t wstride) {
   const int z = blockIdx.y;
-  const int rows = 4 * kap, cols = 4 * dn;
-  const cplx<R>* K = Khat + (int64_t)z * rk * 16;
+  const int rows = d * kap, cols = d * dn, dd = d * d;
+  const cplx<R>* K = Khat + (int64_t)z * rk * dd;
   const cplx<R>* Vz = V + (int64_t)z * vstride;
   cplx<R>* Wz = W + (int64_t)z * wstride;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < rows * cols; e += gridDim.x * blockDim.x) {
     const int i = e / cols, j = e % cols;
     const int pq = i / kap, nu = i % kap, p = j / dn, n = j % dn;
     cplx<R> acc = mk<R>(0, 0);
-    for (int k = 0; k < rk; ++k) cfma(acc, K[k * 16 + pq * 4 + p], Vz[(int64_t)(k * dn + n) + (int64_t)nu * vld]);
+    for (int k = 0; k < rk; ++k) cfma(acc, K[k * dd + pq * d + p], Vz[(int64_t)(k * dn + n) + (int64_t)nu * vld]);
     Wz[e] = acc;
+  }
+}
+
+// V[:, j] *= s[j] for a column-major n x n matrix (FP64)
+__global__ void scale_cols_kernel(int n, cplx<double>* V, const double* s) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n; e += (int64_t)gridDim.x * blockDim.x) {
+    const double f = s[e / n];
+    V[e].x *= f;
+    V[e].y *= f;
   }
 }
 
@@ -394,15 +378,6 @@ cudaError_t fuse_gate(cudaStream_t s, int batch, const FuseArgs<R>& a) {
   return cudaGetLastError();
 }
 template <typename R>
-cudaError_t apply_1q_kraus(cudaStream_t s, int batch, int dl, int dn, int dr, int rk, const cplx<R>* A,
-                           int64_t astride, const cplx<R>* Khat, cplx<R>* X, int64_t xstride) {
-  if (batch <= 0) return cudaSuccess;
-  int64_t total = (int64_t)rk * dn * dl * 2 * dr;
-  dim3 grid(grid_for(total), batch);
-  apply1q_kernel<R><<<grid, NT, 0, s>>>(dl, dn, dr, rk, A, astride, Khat, X, xstride);
-  return cudaGetLastError();
-}
-template <typename R>
 cudaError_t build_T(cudaStream_t s, int batch, int dm, const cplx<R>* Rt, const cplx<R>* E, int64_t estride,
                     cplx<R>* T, int64_t tstride) {
   if (batch <= 0) return cudaSuccess;
@@ -420,22 +395,27 @@ cudaError_t build_Y(cudaStream_t s, int batch, int kchi, int dm, int rk, const c
   build_Y_kernel<R><<<grid, NT, 0, s>>>(kchi, dm, rk, Khat, H, hstride, Y, ystride);
   return cudaGetLastError();
 }
+cudaError_t scale_cols(cudaStream_t s, int n, cplx<double>* V, const double* f) {
+  scale_cols_kernel<<<grid_for((int64_t)n * n), NT, 0, s>>>(n, V, f);
+  return cudaGetLastError();
+}
+
 template <typename R>
-cudaError_t kraus_gram(cudaStream_t s, int batch, int rk, int dn, const cplx<R>* Khat, const cplx<R>* H,
+cudaError_t kraus_gram(cudaStream_t s, int batch, int d, int rk, int dn, const cplx<R>* Khat, const cplx<R>* H,
                        int64_t hstride, cplx<R>* G, int64_t gstride) {
   if (batch <= 0) return cudaSuccess;
-  if (rk > 16) return cudaErrorInvalidValue;
+  if (rk > 16 || (d != 2 && d != 4)) return cudaErrorInvalidValue;
   dim3 grid(grid_for((int64_t)rk * dn * rk * dn), batch);
-  kraus_gram_kernel<R><<<grid, NT, 0, s>>>(rk, dn, Khat, H, hstride, G, gstride);
+  kraus_gram_kernel<R><<<grid, NT, 0, s>>>(d, rk, dn, Khat, H, hstride, G, gstride);
   return cudaGetLastError();
 }
 template <typename R>
-cudaError_t kraus_fold(cudaStream_t s, int batch, int rk, int dn, int kap, const cplx<R>* Khat, const cplx<R>* V,
-                       int64_t vstride, int vld, cplx<R>* W, int64_t wstride) {
+cudaError_t kraus_fold(cudaStream_t s, int batch, int d, int rk, int dn, int kap, const cplx<R>* Khat,
+                       const cplx<R>* V, int64_t vstride, int vld, cplx<R>* W, int64_t wstride) {
   if (batch <= 0) return cudaSuccess;
-  if (rk > 16) return cudaErrorInvalidValue;
-  dim3 grid(grid_for((int64_t)16 * kap * dn), batch);
-  kraus_fold_kernel<R><<<grid, NT, 0, s>>>(rk, dn, kap, Khat, V, vstride, vld, W, wstride);
+  if (rk > 16 || (d != 2 && d != 4)) return cudaErrorInvalidValue;
+  dim3 grid(grid_for((int64_t)d * d * kap * dn), batch);
+  kraus_fold_kernel<R><<<grid, NT, 0, s>>>(d, rk, dn, kap, Khat, V, vstride, vld, W, wstride);
   return cudaGetLastError();
 }
 template <typename R>
@@ -502,17 +482,15 @@ cudaError_t permute(cudaStream_t s, int batch, int nd, const int* dims, const in
 
 #define INST(R)                                                                                                  \
   template cudaError_t fuse_gate<R>(cudaStream_t, int, const FuseArgs<R>&);                                      \
-  template cudaError_t apply_1q_kraus<R>(cudaStream_t, int, int, int, int, int, const cplx<R>*, int64_t,        \
-                                         const cplx<R>*, cplx<R>*, int64_t);                                      \
   template cudaError_t build_T<R>(cudaStream_t, int, int, const cplx<R>*, const cplx<R>*, int64_t, cplx<R>*,     \
                                   int64_t);                                                                      \
   template cudaError_t build_Y<R>(cudaStream_t, int, int, int, int, const cplx<R>*, const cplx<R>*, int64_t,     \
                                   cplx<R>*, int64_t);                                                            \
   template cudaError_t copy_view<R>(cudaStream_t, int, int, int, const cplx<R>*, View, cplx<R>*, View);          \
-  template cudaError_t kraus_gram<R>(cudaStream_t, int, int, int, const cplx<R>*, const cplx<R>*, int64_t,       \
+  template cudaError_t kraus_gram<R>(cudaStream_t, int, int, int, int, const cplx<R>*, const cplx<R>*, int64_t,  \
                                      cplx<R>*, int64_t);                                                         \
-  template cudaError_t kraus_fold<R>(cudaStream_t, int, int, int, int, const cplx<R>*, const cplx<R>*, int64_t,  \
-                                     int, cplx<R>*, int64_t);                                                    \
+  template cudaError_t kraus_fold<R>(cudaStream_t, int, int, int, int, int, const cplx<R>*, const cplx<R>*,      \
+                                     int64_t, int, cplx<R>*, int64_t);                                           \
   template cudaError_t scale_odd<R>(cudaStream_t, int, int64_t, int64_t, R, cplx<R>*, int64_t);                  \
   template cudaError_t init_zero_sites<R>(cudaStream_t, int, cplx<R>*, int64_t);                                 \
   template cudaError_t dot_batch<R>(cudaStream_t, int, int64_t, const cplx<R>*, int64_t, const cplx<R>*,         \

@@ -54,6 +54,7 @@ def lib():
         "apply_1q_batch": [vp, i32, vp, vp, vp],
         "apply_2q_batch": [vp, i32, vp, vp, vp],
         "truncate_kraus": [vp, i32, i32, dp],
+        "truncate_bonds": [vp, i32, dp],
         "expect": [vp, i32, ip, i32, dp],
         "mpdo_save": [vp, C.c_char_p],
         "mpdo_load": [C.c_char_p, vp, C.POINTER(vp)],
@@ -72,6 +73,7 @@ def lib():
         "mpdo_wait_selftest": [i32, ip],
         "mpdo_set_trunc_order": [vp, i32],
         "mpdo_tc_selftest": [i32, i32, i32, dp, ip],
+        "mpdo_fidelity": [vp, i32, vp, i32, dp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -240,6 +242,12 @@ class MPDO:
         _check(lib().truncate_kraus(self.h, q, kappa, out.ctypes.data_as(C.POINTER(C.c_double))), "truncate_kraus")
         return out
 
+    def truncate_bonds(self, chi: int) -> np.ndarray:
+        """Global bond truncation (Sec. II.D): QR sweep into canonical form, every bond cut to chi."""
+        out = np.zeros(self.batch)
+        _check(lib().truncate_bonds(self.h, chi, out.ctypes.data_as(C.POINTER(C.c_double))), "truncate_bonds")
+        return out
+
     # -------------------------------------------------------------- readouts
     def _expect(self, kind: int, args=(), size: Optional[int] = None) -> np.ndarray:
         a = np.asarray(args, dtype=np.int32).reshape(-1)
@@ -281,6 +289,12 @@ class MPDO:
 
     def purity(self):
         return self._expect(PURITY)
+
+    def fidelity(self, other: "MPDO", chain: int = 0, other_chain: int = 0) -> float:
+        """Uhlmann fidelity (Sec. IV.C) of this state's chain against another handle's chain (n <= 7)."""
+        out = C.c_double()
+        _check(lib().mpdo_fidelity(self.h, chain, other.h, other_chain, C.byref(out)), "mpdo_fidelity")
+        return out.value
 
     def discarded(self):
         return self._expect(DISCARDED, size=3 * self.batch).reshape(self.batch, 3)
@@ -362,6 +376,9 @@ def run_circuit(circuit, chi_max: int, kappa_max: int, prec="fp64", stream: int 
     st.set_trunc_order(trunc_order)
     chans = {}
     for op in circuit.ops:
+        if op.kind == 3:
+            st.truncate_bonds(op.q)
+            continue
         ch = chans.get(op.chan)
         if ch is None:
             ch = chans[op.chan] = st.channels(op.kind, [circuit.chis[op.chan][1]])

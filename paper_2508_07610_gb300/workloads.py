@@ -150,11 +150,19 @@ def kraus_to_chi(kraus: Sequence[np.ndarray]) -> np.ndarray:
 @dataclasses.dataclass
 class Op:
     """One noisy gate: `kind` is 1 or 2 (qubits q or q, q+1); U is the ideal gate,
-    `chan` indexes Circuit.chis (the channel applied after the gate)."""
+    `chan` indexes Circuit.chis (the channel applied after the gate).  kind 3 (SWEEP) is no gate but
+    the global bond truncation of Sec. II.D to chi = q, placed at the end of a layer."""
     kind: int
     q: int
     U: np.ndarray
     chan: int
+
+
+SWEEP = 3
+
+
+def sweep_op(chi: int) -> Op:
+    return Op(SWEEP, chi, np.zeros((1, 1), dtype=np.complex128), -1)
 
 
 @dataclasses.dataclass
@@ -285,6 +293,7 @@ def qaoa_maxcut(n: int, p: int, edges, gammas, betas, rng, chis=None, c1=None, c
             cswap.append(_add_chan(chis, 2, compose(depolarizing_2q(2 * p2), unitary_channel(zz_phase(phi)))))
     eset = set((min(a, b), max(a, b)) for a, b in edges)
     ops = [Op(1, q, hadamard(), c1[q]) for q in range(n)]
+    roles = [("h", -1)] * n  # per op: its kind and layer, so the angles can be replaced later
     pos = list(range(n))  # pos[i] = logical vertex at chain position i
     fused_cache = {}
     for layer in range(p):
@@ -305,13 +314,33 @@ def qaoa_maxcut(n: int, p: int, edges, gammas, betas, rng, chis=None, c1=None, c
                         ck = _add_chan(chis, 2, compose(ks, moved))
                         fused_cache[key] = ck
                     ops.append(Op(2, q, U, ck))
+                    roles.append(("cost", layer))
                 else:
                     ops.append(Op(2, q, swap(), cswap[q]))
+                    roles.append(("swap", layer))
                 pos[q], pos[q + 1] = pos[q + 1], pos[q]
         for q in range(n):
             ops.append(Op(1, q, qaoa_mixer(b), c1[q]))
+            roles.append(("mix", layer))
     return _circuit(n, ops, chis, {"name": f"qaoa_n{n}_p{p}", "edges": sorted(eset), "perm": pos,
-                                   "gammas": list(gammas), "betas": list(betas), "noise": record})
+                                   "gammas": list(gammas), "betas": list(betas), "noise": record,
+                                   "roles": roles})
+
+
+def qaoa_with_angles(template: Circuit, gammas, betas) -> Circuit:
+    """The QAOA circuit `template` (from qaoa_maxcut) with other angles: the same gate positions and
+    channels, the cost gates (fused with their SWAP) and mixers rebuilt for gammas, betas."""
+    ops = []
+    for op, (role, layer) in zip(template.ops, template.meta["roles"]):
+        if role == "cost":
+            ops.append(Op(2, op.q, swap() @ qaoa_cost(gammas[layer]), op.chan))
+        elif role == "mix":
+            ops.append(Op(1, op.q, qaoa_mixer(betas[layer]), op.chan))
+        else:
+            ops.append(op)
+    meta = dict(template.meta)
+    meta["gammas"], meta["betas"] = list(gammas), list(betas)
+    return Circuit(template.n, ops, template.chis, template.kraus, meta)
 
 
 def qaoa_batch(count: int, seed: int = MASTER_SEED + 3, n_choices=tuple(range(8, 25, 2)), p_max: int = 4):
@@ -328,6 +357,38 @@ def qaoa_batch(count: int, seed: int = MASTER_SEED + 3, n_choices=tuple(range(8,
         bet = rng.uniform(0, math.pi, size=p)
         out.append(qaoa_maxcut(n, p, edges, gam, bet, rng))
     return out
+
+
+def cnot() -> np.ndarray:
+    """CNOT with the first qubit as control (basis index 2 p_q + p_{q+1})."""
+    m = np.eye(4, dtype=np.complex128)
+    m[2:, 2:] = PX
+    return m
+
+
+def random_rot_cnot(n: int, m: int, rng, chans=None, sweep_chi: int = 0) -> Circuit:
+    """The random 1D circuits of the truncation study (Sec. IV.C, Fig. 13a): a layer of random
+    R in {RX, RY, RZ} with angles U(0, 2 pi] on every qubit, then a layer of CNOTs on the bonds of
+    parity layer % 2, repeated m - 1 times, and a final rotation layer.  Channels as the HEA workload
+    (one realisation per circuit, or the given (chis, c1, c2)).  With sweep_chi > 0 every CNOT layer
+    is followed by the global bond truncation to sweep_chi (the schedule of Sec. II.D)."""
+    chis, c1, c2 = chans if chans is not None else hea_channels(n, rng)
+    rots = (rx, ry, rz)
+    ops = []
+
+    def rot_layer():
+        for q in range(n):
+            r = rots[int(rng.integers(0, 3))]
+            ops.append(Op(1, q, r(2 * math.pi - rng.uniform(0, 2 * math.pi)), c1[q]))
+
+    for layer in range(m - 1):
+        rot_layer()
+        for q in range(layer % 2, n - 1, 2):
+            ops.append(Op(2, q, cnot(), c2[q]))
+        if sweep_chi > 0:
+            ops.append(sweep_op(sweep_chi))
+    rot_layer()
+    return _circuit(n, ops, chis, {"name": f"random_rot_cnot_n{n}_m{m}"})
 
 
 def crosstalk_sweep(n: int = 40, depth: int = 20, seed: int = MASTER_SEED + 4) -> Circuit:

@@ -367,3 +367,36 @@ def test_kraus_first_equals_split_first_without_bond_cuts():
     ra, rb = _oracle_from_gpu(a).dense(), _oracle_from_gpu(b).dense()
     assert np.max(np.abs(ra / np.trace(ra) - rb / np.trace(rb))) < 1e-12
     assert abs(a.discarded()[0, 1] - b.discarded()[0, 1]) < 1e-12
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp32"])
+@pytest.mark.parametrize("n,m,chi,kap,seed", [(5, 6, 3, 4, 12), (6, 8, 4, 4, 15), (6, 6, 2, 2, 2), (6, 8, 1, 4, 3)])
+def test_global_bond_truncation_matches_oracle(prec, n, m, chi, kap, seed):
+    """The paper's schedule of Sec. II.D on the random RX/RY/RZ + CNOT circuits of Fig. 13a: per-gate
+    splits keep every rank (cap 64), and after each CNOT layer a QR sweep into canonical form is
+    followed by the right-to-left truncation of every bond to chi; Kraus legs are truncated per gate."""
+    rng = np.random.default_rng(900 + seed)
+    circ = W.random_rot_cnot(n, m, rng, sweep_chi=chi)
+    st = G.run_circuit(circ, 64, kap, prec)
+    orc = OM.run_circuit(circ, 64, kap)
+    assert orc.discarded_chi > 1e-3
+    assert max(orc.bond_dims()) <= chi and max(st.dims()[0]) <= chi
+    _check_state(st, orc, prec, n, label=f"global sweep n={n} m={m} chi={chi} kappa={kap}")
+
+
+def test_global_bond_truncation_exact_when_chi_covers_ranks():
+    rng = np.random.default_rng(77)
+    circ = W.random_circuit(4, 12, rng, rank1=2, rank2=3)  # Kraus ranks up to 12: kappa_max = 32 cuts nothing
+    st = G.run_circuit(circ, 64, 32, "fp64")
+    before = _oracle_from_gpu(st).dense()
+    w = st.truncate_bonds(64)[0]
+    after = _oracle_from_gpu(st).dense()
+    assert abs(w) < 1e-13
+    assert np.max(np.abs(after - before)) < 1e-12
+    assert np.max(np.abs(after - OD.run_circuit(circ))) < 1e-12
+
+
+def test_global_bond_truncation_rejects_zero_chi():
+    st = G.MPDO(3, 4, 2)
+    with pytest.raises(G.MPDOError):
+        st.truncate_bonds(0)
