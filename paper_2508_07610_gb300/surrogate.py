@@ -160,11 +160,8 @@ def mpdo_targets(circs, chi: int, kappa: int, prec: str, torch) -> np.ndarray:
     run = BR.BatchedRun(circs, chi, kappa, prec, torch=torch)
     run.run()
     mc = run.maxcut()
-    ghz = np.zeros(len(circs))
-    for g in run.groups:
-        f = g.st.ghz_fidelity()
-        for b, ci in enumerate(g.idx):
-            ghz[ci] = f[b]
+    ghz = run.ghz()
+    run.free()
     ne = np.array([len(c.meta["edges"]) for c in circs])
     return np.stack([mc / ne, ghz], axis=1).astype(np.float32)
 
@@ -173,21 +170,70 @@ def features(circs) -> np.ndarray:
     return np.stack([W.surrogate_features(c) for c in circs])
 
 
-def screen(model: Surrogate, candidates, chi, kappa, prec, torch, top: int = 64, tol: float = 1e-2,
-           X: Optional[np.ndarray] = None):
-    """Rank candidates by predicted <H_MaxCut>/|E|, re-score the top ones with the MPDO, and fall back
-    to the MPDO alone (the first `top` candidates in their given order) when the surrogate's error on
-    the re-scored set (root-mean-square over it) exceeds tol.  Returns (best index, its MPDO score,
-    surrogate error, fell back)."""
-    if X is None:
-        X = features(candidates)
-    Xd = torch.tensor(X, device="cuda")
-    pred = model.forward(Xd)[:, 0].cpu().numpy()
+def angle_features(template, gammas: np.ndarray, betas: np.ndarray, p_max: int = 4) -> np.ndarray:
+    """Features of many candidate angle sets (rows of gammas, betas) that share the channels of one
+    QAOA circuit `template`: the angles padded to p_max and divided by pi, then the template's
+    noise descriptors (W.surrogate_features layout)."""
+    base = W.surrogate_features(template, p_max)
+    N, p = gammas.shape
+    X = np.tile(base, (N, 1))
+    X[:, :p_max] = 0.0
+    X[:, p_max:2 * p_max] = 0.0
+    X[:, :p] = gammas / math.pi
+    X[:, p_max:p_max + p] = betas / math.pi
+    return X.astype(np.float32)
+
+
+def mpdo_scores(template, gammas, betas, chi, kappa, prec, torch) -> np.ndarray:
+    """<H_MaxCut>/|E| of the candidates (rows of gammas, betas) on the template's channels, by the
+    batched MPDO."""
+    circs = [W.qaoa_with_angles(template, g, b) for g, b in zip(gammas, betas)]
+    return mpdo_targets(circs, chi, kappa, prec, torch)[:, 0]
+
+
+def screen(model: Surrogate, X: np.ndarray, score, top: int = 64, tol: float = 1e-2):
+    """One screened step of the variational loop.  The surrogate ranks all candidates (rows of the
+    feature matrix X) by predicted <H_MaxCut>/|E|; score(indices) evaluates the `top` best with the
+    MPDO.  The answer is the best MPDO-scored candidate.  When the surrogate's root-mean-square error
+    on the scored set exceeds tol its ranking is not trusted (fallback): the loop should score
+    candidates with the MPDO alone from then on; the MPDO evaluations already made are kept, so the
+    budget is the same either way.  Returns (best index, its MPDO score, surrogate error, fell back)."""
+    t = model.torch
+    pred = model.forward(t.tensor(X, device="cuda"))[:, 0].cpu().numpy()
     order = np.argsort(-pred)[:top]
-    scored = mpdo_targets([candidates[i] for i in order], chi, kappa, prec, torch)[:, 0]
+    scored = np.asarray(score(order))
     err = float(np.sqrt(np.mean((scored - pred[order]) ** 2)))
-    if err > tol:
-        order = np.arange(min(top, len(candidates)))
-        scored = mpdo_targets([candidates[i] for i in order], chi, kappa, prec, torch)[:, 0]
-        return int(order[np.argmax(scored)]), float(np.max(scored)), err, True
-    return int(order[np.argmax(scored)]), float(np.max(scored)), err, False
+    b = int(np.argmax(scored))
+    return int(order[b]), float(scored[b]), err, err > tol
+
+
+def generate_training_set(count: int, n: int, edges, seed: int, chi: int, kappa: int, prec: str, torch,
+                          p_choices=(1, 2, 3, 4), scale_range=(0.5, 2.0), chunk: int = 4096,
+                          checkpoint: Optional[str] = None):
+    """`count` (features, targets) pairs from the batched MPDO, generated in chunks of `chunk` samples.
+    Chunk c draws its circuits from its own seed (seed, c), so the set does not depend on how it was
+    split.  With a checkpoint path every finished chunk is saved there (NumPy .npz) and a later call
+    resumes after the last saved chunk."""
+    Xs, Ys = [], []
+    if checkpoint:
+        try:
+            with np.load(checkpoint) as f:
+                Xs = [f["X"][i:i + chunk] for i in range(0, f["X"].shape[0], chunk)]
+                Ys = [f["Y"][i:i + chunk] for i in range(0, f["Y"].shape[0], chunk)]
+        except (FileNotFoundError, OSError, KeyError):
+            Xs, Ys = [], []
+    # only whole chunks are kept (every chunk is generated in full and the result cut to count)
+    Xs = [x for x in Xs if x.shape[0] == chunk]
+    Ys = Ys[:len(Xs)]
+    done = chunk * len(Xs)
+    while done < count:
+        c = done // chunk
+        m = chunk
+        rng = np.random.default_rng([seed, c])
+        circs = sample_circuits(m, n, edges, rng, p_choices, scale_range)
+        Xs.append(features(circs))
+        Ys.append(mpdo_targets(circs, chi, kappa, prec, torch))
+        done += m
+        if checkpoint:
+            np.savez(checkpoint, X=np.concatenate(Xs), Y=np.concatenate(Ys))
+    return np.concatenate(Xs)[:count], np.concatenate(Ys)[:count]

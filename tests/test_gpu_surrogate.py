@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 from oracle import mlp as OM
+from oracle import mpdo as OMP
 from paper_2508_07610_gb300 import surrogate as S
 from paper_2508_07610_gb300 import workloads as W
 
@@ -79,6 +80,43 @@ def test_forward_matches_bf16_rounded_reference(torch):
     assert model.sync() is None
 
 
+def test_gradients_match_bf16_rounded_reference_element_by_element(torch):
+    """The backward pass against an FP64 evaluation that rounds the input, the weights and every
+    hidden activation to BF16 where the kernels do (pre-activations and deltas stay unrounded, as
+    FP32 on the GPU): every gradient entry within 1e-3 of its layer's largest entry plus 1e-2 of
+    itself (FP32 summation order over the batch and the FP32 pre-activations)."""
+    model = S.Surrogate(torch, max_batch=1024, seed=3)
+    dims = model.dims
+    p = model.params().astype(np.float64)
+    rng = np.random.default_rng(2)
+    X = rng.normal(size=(512, 16)).astype(np.float32)
+    T = rng.normal(scale=0.3, size=(512, 2)).astype(np.float32)
+    model.gradients(torch.tensor(X, device="cuda"), torch.tensor(T, device="cuda"))
+    g = model.grads().astype(np.float64)
+    lay, total = OM.layout(dims)
+    layers = OM.unpack(p, dims)
+    a, hs, zs = _bf16(X), [], []
+    for li, (Wl, bl) in enumerate(layers):
+        hs.append(a)
+        z = a @ _bf16(Wl).T + bl
+        zs.append(z)
+        a = _bf16(OM.gelu(z)) if li + 1 < len(layers) else z
+    d = 2.0 * (a - T) / a.size
+    g_ref = np.zeros(total)
+    for li in range(len(layers) - 1, -1, -1):
+        w, b, i, o = lay[li]
+        g_ref[w:w + i * o] = (d.T @ hs[li]).reshape(-1)
+        g_ref[b:b + o] = d.sum(axis=0)
+        if li > 0:
+            d = (d @ _bf16(layers[li][0])) * OM.gelu_grad(zs[li - 1])
+    for w, b, i, o in lay:
+        for lo, hi in ((w, w + i * o), (b, b + o)):
+            ref = g_ref[lo:hi]
+            lim = 1e-3 * np.max(np.abs(ref)) + 1e-2 * np.abs(ref)
+            bad = np.abs(g[lo:hi] - ref) > lim
+            assert not bad.any(), (lo, int(bad.sum()), float(np.max(np.abs(g[lo:hi] - ref))))
+
+
 def test_training_fits_a_smooth_function(torch):
     rng = np.random.default_rng(1)
     X = rng.uniform(-1, 1, size=(8192, 16)).astype(np.float32)
@@ -89,39 +127,76 @@ def test_training_fits_a_smooth_function(torch):
     assert losses[-1] < 0.05 * losses[0], losses[::5]
 
 
-def test_screened_loop_beats_the_loop_without_the_surrogate(torch):
-    """Train on MPDO-generated samples of noisy p = 1 QAOA on one fixed 8-vertex 3-regular graph (angles
-    and noise strength varied), then with the
-    same MPDO budget (64 re-scored candidates) the surrogate-screened search must find a better
-    <H_MaxCut> than scoring 64 unscreened candidates."""
+def test_training_data_generation_resumes_from_its_checkpoint(torch, tmp_path):
+    """Chunked MPDO data generation saved after every chunk: an interrupted run resumed from the
+    checkpoint gives the same set as an uninterrupted one."""
+    rng = np.random.default_rng(3)
+    n = 6
+    edges = W.random_regular3(n, rng)
+    ck = str(tmp_path / "data.npz")
+    X1, Y1 = S.generate_training_set(2048, n, edges, 5, 8, 4, "mixed", torch, chunk=1024, checkpoint=ck)
+    X2, Y2 = S.generate_training_set(3072, n, edges, 5, 8, 4, "mixed", torch, chunk=1024, checkpoint=ck)
+    X3, Y3 = S.generate_training_set(3072, n, edges, 5, 8, 4, "mixed", torch, chunk=1024)
+    assert X2.shape == (3072, 16) and np.array_equal(X2[:2048], X1) and np.array_equal(Y2[:2048], Y1)
+    assert np.array_equal(X2, X3) and np.max(np.abs(Y2 - Y3)) < 1e-6
+
+
+def test_screened_loop_reaches_the_oracle_verified_optimum_faster(torch):
+    """Config 5's loop on noisy p = 1 QAOA over one 8-vertex 3-regular graph: the surrogate, trained
+    on MPDO samples, screens 65,536 candidate angle sets; the MPDO re-scores the top 64; the surrogate
+    must stay within the 1e-2 error bound on them (no fallback).  The loop without the surrogate
+    scores the same candidates in their given order with the MPDO, 4,096 at a time, until it reaches
+    the screened loop's optimum, which the CPU oracle verifies; the screened loop must take less wall
+    time.  Both times are printed."""
+    import time
     rng = np.random.default_rng(W.MASTER_SEED + 5)
     n = 8
     edges = W.random_regular3(n, rng)
     chi, kap, prec = 16, 4, "mixed"
-    train = S.sample_circuits(4096, n, edges, rng, p_choices=(1,))
-    Y = S.mpdo_targets(train, chi, kap, prec, torch)
-    X = S.features(train)
-    model = S.Surrogate(torch, max_batch=4096, seed=11)
-    Xd, Yd = torch.tensor(X, device="cuda"), torch.tensor(Y, device="cuda")
-    losses = model.train(Xd, Yd, epochs=400, batch=256, lr=2e-3)
-    assert losses[-1] < 0.1 * losses[0]
-    # held-out error of the surrogate
-    test = S.sample_circuits(256, n, edges, rng, p_choices=(1,))
-    Yt = S.mpdo_targets(test, chi, kap, prec, torch)
-    pt = model.forward(torch.tensor(S.features(test), device="cuda")).cpu().numpy()
-    rmse = float(np.sqrt(np.mean((pt[:, 0] - Yt[:, 0]) ** 2)))
-    print(f"surrogate held-out RMSE of <H_MaxCut>/|E|: {rmse:.4f}, final training loss {losses[-1]:.2e}")
-    assert rmse < 0.05
-    # screening: candidates at one noise setting, p = 1
-    cand = []
+    X, Y = S.generate_training_set(16384, n, edges, 17, chi, kap, prec, torch, p_choices=(1,),
+                                   scale_range=(0.8, 1.25), chunk=8192)
+    model = S.Surrogate(torch, max_batch=65536, seed=11)
+    losses = model.train(torch.tensor(X, device="cuda"), torch.tensor(Y, device="cuda"), epochs=300, batch=512,
+                         lr=2e-3)
+    assert losses[-1] < 0.05 * losses[0]
+    # one noise realisation at the nominal strengths; 65,536 random angle sets on it
+    template = W.qaoa_maxcut(n, 1, edges, [0.3], [0.4], np.random.default_rng(123), scale=1.0)
     crng = np.random.default_rng(99)
-    for _ in range(2048):
-        g = crng.uniform(0, math.pi, size=1)
-        b = crng.uniform(0, math.pi, size=1)
-        cand.append(W.qaoa_maxcut(n, 1, edges, g, b, np.random.default_rng(7), scale=1.0))
-    best_i, best_screened, err, fell_back = S.screen(model, cand, chi, kap, prec, torch, top=64, tol=0.05)
-    unscreened = S.mpdo_targets(cand[:64], chi, kap, prec, torch)[:, 0]
-    print(f"screened best {best_screened:.4f} (surrogate error {err:.3f}, fallback {fell_back}) "
-          f"vs unscreened best {unscreened.max():.4f}")
-    assert not fell_back
-    assert best_screened > unscreened.max()
+    G_ = crng.uniform(0, math.pi, size=(65536, 1))
+    B_ = crng.uniform(0, math.pi, size=(65536, 1))
+    Xc = S.angle_features(template, G_, B_)
+    Xt = S.angle_features(template, G_[:512], B_[:512])
+    yt = S.mpdo_scores(template, G_[:512], B_[:512], chi, kap, prec, torch)
+    pt = model.forward(torch.tensor(Xt, device="cuda"))[:, 0].cpu().numpy()
+    print(f"held-out RMSE of <H_MaxCut>/|E| at the screening noise: {np.sqrt(np.mean((pt - yt) ** 2)):.4f}")
+
+    def score(idx):
+        return S.mpdo_scores(template, G_[idx], B_[idx], chi, kap, prec, torch)
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    best_i, best, err, fell_back = S.screen(model, Xc, score, top=64, tol=1e-2)
+    t_screened = time.perf_counter() - t0
+    # the optimum, verified by the oracle on the CPU
+    circ = W.qaoa_with_angles(template, G_[best_i], B_[best_i])
+    o = OMP.run_circuit(circ, chi, kap)
+    pos = {v: i for i, v in enumerate(circ.meta["perm"])}
+    ref = o.maxcut([(pos[u], pos[v]) for u, v in circ.meta["edges"]]) / len(circ.meta["edges"])
+    assert abs(ref - best) < 1e-6
+    # the loop without the surrogate, to the same optimum
+    t0 = time.perf_counter()
+    reached, scored = None, 0
+    for c0 in range(0, 65536, 4096):
+        s = score(np.arange(c0, c0 + 4096))
+        scored += 4096
+        # the same circuit scored in another batch may round differently: both scores are within the
+        # 1e-6 parity bound of the oracle's value
+        if s.max() >= best - 2e-6:
+            reached = float(s.max())
+            break
+    t_plain = time.perf_counter() - t0
+    print(f"screened: optimum {best:.5f} (oracle {ref:.5f}) in {t_screened:.2f} s with 64 MPDO evaluations, "
+          f"surrogate error {err:.4f}; without the surrogate: {reached} after {scored} MPDO evaluations in "
+          f"{t_plain:.2f} s; speed-up {t_plain / t_screened:.1f}x")
+    assert not fell_back and err <= 1e-2
+    assert reached is not None and t_screened < t_plain
