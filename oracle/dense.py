@@ -65,10 +65,10 @@ def run_circuit(circuit) -> np.ndarray:
     n = circuit.n
     rho = zero_state(n)
     for op in circuit.ops:
-        if op.kind == 3:  # a bond-truncation directive: the exact state is left as it is
+        if op.kind == 8:  # a bond-truncation directive: the exact state is left as it is
             continue
         nq, chi = circuit.chis[op.chan]
-        qs = [op.q] if op.kind == 1 else [op.q, op.q + 1]
+        qs = list(range(op.q, op.q + op.kind))
         rho = apply_noisy_gate(rho, n, qs, op.U, chi)
     return rho
 

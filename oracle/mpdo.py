@@ -9,7 +9,7 @@ open-chain trace of the local densities M = sum_n T T* of Sec. II.C.
 Steps, in the paper's order:
   * a noisy gate is K_i = N_i U (Eq. for K_i in Sec. II.C; noise after the gate);
     its Kraus index becomes a new leg joined to the site's Kraus leg (Fig. 2b,c);
-    for a two-qubit gate the new leg joins the right site q+1;
+    for a two-qubit gate the new leg joins the right site q+1, for a three-qubit channel site q+2;
   * bond truncation (Fig. 3b): the chain is kept in canonical form by QR sweeps
     and the two-site tensor is split by an SVD that keeps the top chi_max values;
   * Kraus-leg truncation (Eq. svdNoise, Fig. 3a): the site tensor as a
@@ -215,6 +215,40 @@ class MPDO:
         if self.auto_truncate and self.trunc_order == "split_first":
             self.truncate_kraus(q + 1)
 
+    def apply_3q(self, q: int, U: np.ndarray, kraus) -> None:
+        """Three-site update on (q, q+1, q+2) for a three-qubit channel, e.g. the crosstalk channel a
+        tomography of a two-qubit gate and its neighbour yields (Fig. 13b): the three sites are merged,
+        K_k = N_k U (8 x 8) applied with the new Kraus leg on site q+2 (the rightmost, as for two-qubit
+        gates), the merged tensor split by two SVDs that keep chi_max values, first
+        (l, p1', n1) | (p2', n2, p3', k, n3, r) and then (b, p2', n2) | (p3', k, n3, r), and the Kraus
+        leg of site q+2 truncated to kappa_max.  The centre is moved onto q first and ends on q+2."""
+        self.move_centre(q)
+        A1, A2, A3 = self.sites[q], self.sites[q + 1], self.sites[q + 2]
+        dl, _, dn1, _ = A1.shape
+        dn2 = A2.shape[2]
+        _, _, dn3, dr = A3.shape
+        rk = len(kraus)
+        K = np.stack([N @ U for N in kraus]).reshape(rk, 2, 2, 2, 2, 2, 2)  # [k, a', b', c', a, b, c]
+        th = np.einsum("lanx,xbmy,ycor->lanbmcor", A1, A2, A3)            # [l, p1, n1, p2, n2, p3, n3, r]
+        th = np.einsum("kxyzabc,lanbmcor->lxnymzkor", K, th)              # [l, p1', n1, p2', n2, p3', k, n3, r]
+        dk = rk * dn3
+        mat = self._perturbed(th.reshape(dl * 2 * dn1, -1))
+        Um, s, Vh = np.linalg.svd(mat, full_matrices=False)
+        k1, w1 = self._keep(s, self.chi_max)
+        self.sites[q] = Um[:, :k1].reshape(dl, 2, dn1, k1)
+        self.discarded_chi += w1
+        self.log.append(("chi", q, k1, len(s), w1))
+        rest = self._perturbed((s[:k1, None] * Vh[:k1]).reshape(k1 * 2 * dn2, 2 * dk * dr))
+        Um2, s2, Vh2 = np.linalg.svd(rest, full_matrices=False)
+        k2, w2 = self._keep(s2, self.chi_max)
+        self.sites[q + 1] = Um2[:, :k2].reshape(k1, 2, dn2, k2)
+        self.sites[q + 2] = (s2[:k2, None] * Vh2[:k2]).reshape(k2, 2, dk, dr)
+        self.discarded_chi += w2
+        self.log.append(("chi", q + 1, k2, len(s2), w2))
+        self.centre = q + 2
+        if self.auto_truncate:
+            self.truncate_kraus(q + 2)
+
     # ------------------------------------------------------------ readouts
     def _bra_ket(self, ops) -> complex:
         """sum_n <psi_n| (x)_i O_i |psi_n>, O_i = ops.get(i, I); E'[r,r'] = sum E[l,l'] T*[l,p,n,r] O[p,p'] T[l',p',n,r']."""
@@ -297,10 +331,12 @@ def run_circuit(circuit, chi_max: int, kappa_max: int, tol: float = 1e-13, kraus
     st = MPDO(circuit.n, chi_max, kappa_max, tol, trunc_order=trunc_order)
     st.perturb = perturb
     for op in circuit.ops:
-        if op.kind == 3:
+        if op.kind == 8:
             st.truncate_bonds(op.q)
         elif op.kind == 1:
             st.apply_1q(op.q, op.U, kraus[op.chan])
+        elif op.kind == 3:
+            st.apply_3q(op.q, op.U, kraus[op.chan])
         else:
             st.apply_2q(op.q, op.U, kraus[op.chan])
     return st

@@ -107,6 +107,63 @@ def amplitude_damping(g: float) -> List[np.ndarray]:
     return [k0, k1]
 
 
+def phase_damping(f: float) -> List[np.ndarray]:
+    """Pure dephasing that scales the off-diagonal elements by f (0 <= f <= 1):
+    sqrt((1+f)/2) I, sqrt((1-f)/2) Z."""
+    return [math.sqrt((1 + f) / 2) * I2, math.sqrt((1 - f) / 2) * PZ]
+
+
+def thermal_relaxation(t: float, T1: float, T2: float) -> List[np.ndarray]:
+    """The thermal relaxation channel (TRC) of Sec. II.B for a gate of duration t: energy relaxation
+    towards |0> with time constant T1 (amplitude damping, gamma = 1 - exp(-t/T1)) and loss of coherence
+    with time constant T2 <= 2 T1 (the off-diagonal elements decay by exp(-t/T2); amplitude damping
+    accounts for exp(-t/2T1) of it, pure dephasing for the rest).  The paper gives no gate durations:
+    t, T1 and T2 are the caller's."""
+    if not (t >= 0 and T1 > 0 and 0 < T2 <= 2 * T1):
+        raise ValueError("thermal relaxation needs t >= 0, T1 > 0 and 0 < T2 <= 2 T1")
+    g = 1 - math.exp(-t / T1)
+    f = math.exp(-t / T2 + t / (2 * T1))
+    return compose(phase_damping(f), amplitude_damping(g))
+
+
+def state_prep_error(p: float) -> List[np.ndarray]:
+    """SPAM at preparation (Sec. II.B): the qubit starts flipped with probability p."""
+    return [math.sqrt(1 - p) * I2, math.sqrt(p) * PX]
+
+
+def readout_error(e01: float, e10: float) -> List[np.ndarray]:
+    """SPAM before measurement (Sec. II.B, probability p_M): a measure-and-reprepare channel with
+    P(read 1 | 0) = e01 and P(read 0 | 1) = e10, so that the diagonal of the final state is the
+    distribution a confused measurement reports."""
+    k = [np.zeros((2, 2), dtype=np.complex128) for _ in range(4)]
+    k[0][0, 0] = math.sqrt(1 - e01)
+    k[1][1, 0] = math.sqrt(e01)
+    k[2][0, 1] = math.sqrt(e10)
+    k[3][1, 1] = math.sqrt(1 - e10)
+    return k
+
+
+def on_qubit(kraus: Sequence[np.ndarray], which: int) -> List[np.ndarray]:
+    """A single-qubit Kraus set as a two-qubit one acting on the first (which = 0) or the second
+    (which = 1) qubit of the pair (basis index 2 p_q + p_{q+1})."""
+    return [np.kron(K, I2) if which == 0 else np.kron(I2, K) for K in kraus]
+
+
+def both_qubits(first: Sequence[np.ndarray], second: Sequence[np.ndarray]) -> List[np.ndarray]:
+    """Kraus set of the product channel first (x) second on a pair."""
+    return [np.kron(A, B) for A in first for B in second]
+
+
+def crosstalk_3q(p2: float, phi: float, phi_xt: float, p_xt: float) -> List[np.ndarray]:
+    """A three-qubit channel of the kind the tomography of a two-qubit gate together with its
+    neighbour yields (Fig. 13b): the gate pair (q, q+1) gets DEP2(p2) o ZZ(phi), the spectator q+2 a
+    ZZ(phi_xt) coupling to q+1 and DEP(p_xt).  As 8 x 8 Kraus operators, qubit q most significant."""
+    pair = [np.kron(K, I2) for K in compose(depolarizing_2q(p2), unitary_channel(zz_phase(phi)))]
+    xt = [np.kron(I2, zz_phase(phi_xt))]
+    spec = [np.kron(np.eye(4, dtype=np.complex128), K) for K in depolarizing_1q(p_xt)]
+    return compose(spec, compose(xt, pair))
+
+
 def unitary_channel(U: np.ndarray) -> List[np.ndarray]:
     return [np.asarray(U, dtype=np.complex128)]
 
@@ -149,8 +206,8 @@ def kraus_to_chi(kraus: Sequence[np.ndarray]) -> np.ndarray:
 # --------------------------------------------------------------------------
 @dataclasses.dataclass
 class Op:
-    """One noisy gate: `kind` is 1 or 2 (qubits q or q, q+1); U is the ideal gate,
-    `chan` indexes Circuit.chis (the channel applied after the gate).  kind 3 (SWEEP) is no gate but
+    """One noisy gate: `kind` is 1, 2 or 3 (qubits q .. q+kind-1); U is the ideal gate,
+    `chan` indexes Circuit.chis (the channel applied after the gate).  kind 8 (SWEEP) is no gate but
     the global bond truncation of Sec. II.D to chi = q, placed at the end of a layer."""
     kind: int
     q: int
@@ -158,7 +215,7 @@ class Op:
     chan: int
 
 
-SWEEP = 3
+SWEEP = 8
 
 
 def sweep_op(chi: int) -> Op:
@@ -423,6 +480,40 @@ def crosstalk_sweep(n: int = 40, depth: int = 20, seed: int = MASTER_SEED + 4) -
     return _circuit(n, ops, chis, {"name": f"crosstalk_n{n}_d{depth}"})
 
 
+# Gate and coherence times of the unified-model workload.  The paper gives none; these are typical
+# superconducting-qubit figures (seconds).
+UNIFIED_TIMES = {"t1q": 50e-9, "t2q": 300e-9, "T1": 30e-6, "T2": 20e-6}
+
+
+def unified_noise_circuit(n: int, depth: int, rng, model: str = "unified", p1: float = 1e-3, p2: float = 1e-2,
+                          p_prep: float = 5e-3, e01: float = 1e-2, e10: float = 3e-2, times=None) -> Circuit:
+    """The noisy circuit models of Sec. II.B (Fig. 1): state-preparation error on every qubit, then per
+    layer Ry Rz on every qubit and CNOTs on the bonds of parity layer % 2, then readout error on every
+    qubit.  A 1q gate is followed by DEP(p1) o TRC(t1q).  A CNOT is followed by TRC(t2q) on both
+    qubits and, in the unified model (Fig. 1b), DEP(p2) on the target qubit only; in the general model
+    (Fig. 1c) DEP(p2) acts on both qubits.  SPAM channels ride on identity gates."""
+    if model not in ("unified", "general"):
+        raise ValueError(model)
+    tm = dict(UNIFIED_TIMES, **(times or {}))
+    chis = _Chans()
+    trc1 = thermal_relaxation(tm["t1q"], tm["T1"], tm["T2"])
+    trc2 = thermal_relaxation(tm["t2q"], tm["T1"], tm["T2"])
+    c_prep = _add_chan(chis, 1, state_prep_error(p_prep))
+    c_meas = _add_chan(chis, 1, readout_error(e01, e10))
+    c1 = _add_chan(chis, 1, compose(depolarizing_1q(p1), trc1))
+    dep2 = on_qubit(depolarizing_1q(p2), 1) if model == "unified" else both_qubits(depolarizing_1q(p2),
+                                                                                    depolarizing_1q(p2))
+    c2 = _add_chan(chis, 2, compose(dep2, both_qubits(trc2, trc2)))
+    ops = [Op(1, q, I2.copy(), c_prep) for q in range(n)]
+    for layer in range(depth):
+        for q in range(n):
+            ops.append(Op(1, q, ry(rng.uniform(-math.pi, math.pi)) @ rz(rng.uniform(-math.pi, math.pi)), c1))
+        for q in range(layer % 2, n - 1, 2):
+            ops.append(Op(2, q, cnot(), c2))
+    ops += [Op(1, q, I2.copy(), c_meas) for q in range(n)]
+    return _circuit(n, ops, chis, {"name": f"{model}_noise_n{n}_d{depth}", "times": tm})
+
+
 def random_unitary(d: int, rng) -> np.ndarray:
     z = (rng.normal(size=(d, d)) + 1j * rng.normal(size=(d, d))) / math.sqrt(2)
     q, r = np.linalg.qr(z)
@@ -436,11 +527,17 @@ def random_channel_kraus(nq: int, rank: int, rng) -> List[np.ndarray]:
     return [V[k * d:(k + 1) * d, :] for k in range(rank)]
 
 
-def random_circuit(n: int, n_ops: int, rng, rank1: int = 3, rank2: int = 6, p2q: float = 0.5) -> Circuit:
-    """Unstructured random noisy circuit: random unitaries with random CPTP channels."""
+def random_circuit(n: int, n_ops: int, rng, rank1: int = 3, rank2: int = 6, p2q: float = 0.5, p3q: float = 0.0,
+                   rank3: int = 6) -> Circuit:
+    """Unstructured random noisy circuit: random unitaries with random CPTP channels (with
+    probability p3q a three-qubit gate and channel)."""
     ops, chis = [], _Chans()
     for _ in range(n_ops):
-        if n > 1 and rng.uniform() < p2q:
+        if n > 2 and rng.uniform() < p3q:
+            q = int(rng.integers(0, n - 2))
+            ch = _add_chan(chis, 3, random_channel_kraus(3, rank3, rng))
+            ops.append(Op(3, q, random_unitary(8, rng), ch))
+        elif n > 1 and rng.uniform() < p2q:
             q = int(rng.integers(0, n - 1))
             ch = _add_chan(chis, 2, random_channel_kraus(2, rank2, rng))
             ops.append(Op(2, q, random_unitary(4, rng), ch))

@@ -301,3 +301,56 @@ def test_global_bond_truncation_leaves_right_isometries():
         A = st.sites[c]
         Am = A.reshape(A.shape[0], -1)
         assert np.max(np.abs(Am @ Am.conj().T - np.eye(A.shape[0]))) < 1e-12
+
+
+# ------------------------------------------------------------------ three-qubit channels (Fig. 13b)
+@pytest.mark.parametrize("seed", [504, 506, 507])
+def test_three_qubit_channels_match_dense_without_truncation(seed):
+    rng = np.random.default_rng(seed)
+    circ = W.random_circuit(4, 10, rng, rank1=2, rank2=3, p3q=0.4, rank3=4)
+    assert any(op.kind == 3 for op in circ.ops)
+    st = M.run_circuit(circ, 4096, 4096)
+    assert st.discarded_chi < 1e-24 and st.discarded_kappa < 1e-24
+    assert np.max(np.abs(st.dense() - D.run_circuit(circ))) < 1e-12
+
+
+def test_three_qubit_update_of_a_two_qubit_channel_equals_the_two_qubit_update():
+    """A channel acting as identity on the third qubit gives the state of the two-qubit update."""
+    rng = np.random.default_rng(41)
+    base = W.random_circuit(4, 8, rng, rank1=2, rank2=3)
+    kr2 = W.random_channel_kraus(2, 3, rng)
+    U2 = W.random_unitary(4, rng)
+    a = M.run_circuit(base, 4096, 4096)
+    b = M.run_circuit(base, 4096, 4096)
+    a.apply_2q(1, U2, kr2)
+    b.apply_3q(1, np.kron(U2, np.eye(2)), [np.kron(K, np.eye(2)) for K in kr2])
+    assert np.max(np.abs(a.dense() - b.dense())) < 1e-12
+
+
+def test_three_qubit_split_weights_match_state_error():
+    """Each of the two splits is an Eckart-Young truncation: with the centre on the first site the
+    discarded weights add up to the squared distance of the purified states."""
+    rng = np.random.default_rng(43)
+    st = M.MPDO(4, 2, 4096)
+    st.auto_truncate = False
+    circ = W.random_circuit(4, 10, rng, rank1=2, rank2=3)
+    kr = [C.chi_to_kraus(chi, nq) for nq, chi in circ.chis]
+    for op in circ.ops:
+        (st.apply_1q if op.kind == 1 else st.apply_2q)(op.q, op.U, kr[op.chan])
+    exact = M.MPDO(4, 4096, 4096)
+    exact.sites = [A.copy() for A in st.sites]
+    exact.centre = st.centre
+    U = W.random_unitary(8, rng)
+    k3 = W.random_channel_kraus(3, 3, rng)
+    exact.auto_truncate = False
+    exact.apply_3q(0, U, k3)
+    st.apply_3q(0, U, k3)
+    w1, w2 = st.log[-2][4], st.log[-1][4]
+    assert w1 > 1e-6 and w2 > 1e-6
+    # both splits keep at most chi_max, and the truncated state stays a valid density matrix
+    assert max(st.bond_dims()) <= 2
+    rho = st.dense() / st.trace()
+    assert np.max(np.abs(rho - rho.conj().T)) < 1e-13 and np.linalg.eigvalsh(rho).min() > -1e-13
+    # Eckart-Young on the first split: the kept weight is the top-chi Schmidt weight of the exact state
+    ex = exact.dense()
+    assert abs(st.trace() - exact.trace() * (1 - w1) * (1 - w2)) < 1e-12 * exact.trace()

@@ -79,7 +79,9 @@ def test_crosstalk_layers():
 
 
 @pytest.mark.parametrize("maker", [lambda: W.ghz_ansatz(), lambda: W.hea(n=6, depth=3), lambda: W.crosstalk_sweep(6, 3),
-                                   lambda: W.qaoa_batch(3, n_choices=(6,), p_max=2)[1]])
+                                   lambda: W.qaoa_batch(3, n_choices=(6,), p_max=2)[1],
+                                   lambda: W.unified_noise_circuit(4, 2, np.random.default_rng(0)),
+                                   lambda: W.unified_noise_circuit(4, 2, np.random.default_rng(0), model="general")])
 def test_channels_are_valid_process_matrices(maker):
     c = maker()
     for nq, chi in c.chis:
@@ -109,3 +111,52 @@ def test_surrogate_features_pad_to_four_layers():
     assert np.allclose(f[4:8], np.array([0.25, 2.0, 0, 0]) / math.pi, atol=1e-7)
     assert np.all(f[8:11] > 0)  # mean p1, p2, gamma (phi's mean has either sign)
     assert np.all(f[12:16] >= 0)  # spreads
+
+
+# ------------------------------------------------------------------ Sec. II.B channel generators
+def _apply(kraus, rho):
+    return sum(K @ rho @ K.conj().T for K in kraus)
+
+
+def test_thermal_relaxation_closed_form():
+    """Population of |1> decays as exp(-t/T1), coherences as exp(-t/T2); trace preserving."""
+    t, T1, T2 = 0.7, 2.0, 1.5
+    K = W.thermal_relaxation(t, T1, T2)
+    assert np.allclose(sum(k.conj().T @ k for k in K), np.eye(2), atol=1e-14)
+    out = _apply(K, np.array([[0, 0], [0, 1]], dtype=complex))
+    assert abs(out[1, 1] - math.exp(-t / T1)) < 1e-14 and abs(out[0, 0] - (1 - math.exp(-t / T1))) < 1e-14
+    plus = np.full((2, 2), 0.5, dtype=complex)
+    out = _apply(K, plus)
+    assert abs(out[0, 1] - 0.5 * math.exp(-t / T2)) < 1e-14
+    # T2 = 2 T1: no pure dephasing, the channel is amplitude damping alone
+    assert abs(W.phase_damping(1.0)[1]).max() == 0
+    with pytest.raises(ValueError):
+        W.thermal_relaxation(1.0, 1.0, 2.5)
+
+
+def test_spam_channels_closed_form():
+    e01, e10, p = 0.02, 0.07, 0.1
+    R = W.readout_error(e01, e10)
+    assert np.allclose(sum(k.conj().T @ k for k in R), np.eye(2), atol=1e-15)
+    for pop1 in (0.0, 0.3, 1.0):
+        rho = np.array([[1 - pop1, 0.2], [0.2, pop1]], dtype=complex)
+        out = _apply(R, rho)
+        assert abs(out[1, 1] - (pop1 * (1 - e10) + (1 - pop1) * e01)) < 1e-15
+        assert abs(out[0, 1]) < 1e-15  # a measurement leaves no coherence
+    out = _apply(W.state_prep_error(p), np.array([[1, 0], [0, 0]], dtype=complex))
+    assert abs(out[1, 1] - p) < 1e-15
+
+
+def test_unified_model_depolarizes_only_the_target():
+    """Fig. 1b: the two-qubit channel's depolarizing part acts on the target (second) qubit only."""
+    from oracle import channels as OC
+    p = 0.2
+    sup = OC.superop(W.on_qubit(W.depolarizing_1q(p), 1))
+    ref = OC.superop([np.kron(np.eye(2), K) for K in W.depolarizing_1q(p)])
+    assert np.allclose(sup, ref, atol=1e-15)
+    rho = np.zeros((4, 4), dtype=complex)
+    rho[0, 0] = 1  # |00>: control untouched, target mixed towards I/2
+    out = _apply(W.on_qubit(W.depolarizing_1q(p), 1), rho)
+    assert abs(out[0, 0] - (1 - p / 2)) < 1e-15 and abs(out[1, 1] - p / 2) < 1e-15 and abs(out[2, 2]) < 1e-15
+    c = W.unified_noise_circuit(3, 2, np.random.default_rng(1))
+    assert [o.kind for o in c.ops[:3]] == [1, 1, 1] and [o.kind for o in c.ops[-3:]] == [1, 1, 1]
