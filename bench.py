@@ -674,7 +674,7 @@ def main():
     ap.add_argument("--groups", type=int, default=4, help="handles (streams) the chains are split over")
     ap.add_argument("--saturate", type=int, default=12)
     ap.add_argument("--plain-steps", type=int, default=1)
-    ap.add_argument("--cpu-updates", type=int, default=1)
+    ap.add_argument("--cpu-updates", type=int, default=4)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp32", "fp64"],
                     help="headline precision: mixed = complex64 contractions with FP64 truncation eigensolvers")

@@ -259,7 +259,7 @@ mpdo_status mpdo_wait_selftest(int limit_us, int* status_out);
  * is stored in the file as JSON; entries found in the file are used without timing.  All host arrays
  * are copied.  MPDO_EINVAL for inconsistent arrays; the channel checks of
  * channel_set_from_process_matrices apply (MPDO_ENOTCP, MPDO_ENOTTP). */
-enum { MPDO_OP_TRUNCATE_BONDS = 3 };
+enum { MPDO_OP_TRUNCATE_BONDS = 8 };
 mpdo_status mpdo_batch_create(int count, const int* n_qubits, const int* op_begin, const int* op_kind, const int* op_q,
                               const double* op_U, const int* op_chi, int n_chi, const int* chi_nq, const double* chis,
                               int chi_max, int kappa_max, int prec, const char* tuning_path, mpdo_batch_t* out);

@@ -64,8 +64,8 @@ class BatchedRun:
         for ci, c in enumerate(self.circuits):
             begin[ci + 1] = begin[ci] + len(c.ops)
             for op in c.ops:
-                if op.kind == 3:  # global bond truncation to chi = op.q: no gate, no channel
-                    kinds.append(3)
+                if op.kind == 8:  # global bond truncation to chi = op.q: no gate, no channel
+                    kinds.append(8)
                     qs.append(op.q)
                     chi_of.append(0)
                     Us.append(np.zeros(16, dtype=np.complex128))

@@ -376,7 +376,7 @@ def run_circuit(circuit, chi_max: int, kappa_max: int, prec="fp64", stream: int 
     st.set_trunc_order(trunc_order)
     chans = {}
     for op in circuit.ops:
-        if op.kind == 3:
+        if op.kind == 8:
             st.truncate_bonds(op.q)
             continue
         ch = chans.get(op.chan)

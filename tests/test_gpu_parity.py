@@ -400,3 +400,30 @@ def test_global_bond_truncation_rejects_zero_chi():
     st = G.MPDO(3, 4, 2)
     with pytest.raises(G.MPDOError):
         st.truncate_bonds(0)
+
+
+# ------------------------------------------------------------------ the noise models of Sec. II.B (Fig. 1)
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp32"])
+@pytest.mark.parametrize("model", ["unified", "general"])
+def test_noise_models_of_fig1_match_oracle(prec, model):
+    """State-preparation error, thermal relaxation after every gate, depolarizing on the CNOT's target
+    only (unified) or on both qubits (general), readout error before measurement."""
+    circ = W.unified_noise_circuit(6, 4, np.random.default_rng(1000), model=model)
+    st = G.run_circuit(circ, 16, 4, prec)
+    orc = OM.run_circuit(circ, 16, 4)
+    assert orc.discarded_kappa > 0
+    _check_state(st, orc, prec, circ.n, label=f"{model} noise model")
+
+
+def test_spam_distribution_closed_form():
+    """With no gates between them, preparation and readout errors give a product distribution with
+    P(read 1) = p (1 - e10) + (1 - p) e01 on every qubit."""
+    n, p, e01, e10 = 3, 0.1, 0.02, 0.07
+    chis = [(1, W.kraus_to_chi(W.state_prep_error(p))), (1, W.kraus_to_chi(W.readout_error(e01, e10)))]
+    ops = [W.Op(1, q, np.eye(2), 0) for q in range(n)] + [W.Op(1, q, np.eye(2), 1) for q in range(n)]
+    st = G.run_circuit(W.Circuit(n, ops, chis), 4, 4, "fp64")
+    p1 = p * (1 - e10) + (1 - p) * e01
+    for z in range(2 ** n):
+        bits = [(z >> (n - 1 - i)) & 1 for i in range(n)]
+        ref = np.prod([p1 if b else 1 - p1 for b in bits])
+        assert abs(st.probability(bits)[0] - ref) < 1e-12
