@@ -87,7 +87,8 @@ mpdo_status mpdo_sync(mpdo_t h);
 
 /* chi -> Kraus (Sec. III): Lambda = sum_mn chi_mn |s_m>><<s_n|, Lambda = sum_i eta_i |psi_i><psi_i|,
  * K_i = sqrt(eta_i) unvec(psi_i), in descending eta; eta <= tol * max eta is pruned (tol <= 0 means
- * 1e-12).  chi: host, (4^nq x 4^nq) complex per channel, `count` channels back to back.  Checks:
+ * 1e-12).  nq = 1, 2 or 3 (three-qubit channels for apply_3q).  chi: host, (4^nq x 4^nq) complex per
+ * channel, `count` channels back to back.  Checks:
  * Hermitian and finite (EINVAL), |Tr chi - 1| <= 1e-8 and sum K^H K = I within 1e-8 (ENOTTP),
  * negative Choi mass <= 1e-8 (ENOTCP).  n_kraus (host, nullable) receives count ranks.  The Kraus
  * sets are padded with zero operators to the largest rank of the set. */
@@ -95,7 +96,8 @@ mpdo_status channel_from_process_matrix(mpdo_t h, int nq, const double* chi, dou
                                         int* n_kraus);
 mpdo_status channel_set_from_process_matrices(mpdo_t h, int nq, int count, const double* chi, double tol,
                                               mpdo_chan_t* out, int* n_kraus);
-/* Copy channel idx's Kraus operators (padded count r_pad x d x d complex) to host `out`. */
+/* Copy channel idx's Kraus operators (r_pad x d x d complex, r_pad = the largest rank of the set) to
+ * host `out`, which must hold that many. */
 mpdo_status channel_kraus(mpdo_chan_t ch, int idx, double* out, int* r_pad);
 mpdo_status channel_free(mpdo_chan_t ch);
 
@@ -107,11 +109,22 @@ mpdo_status apply_1q(mpdo_t h, int q, const double* U, mpdo_chan_t ch);
  * channel applied with the new Kraus leg on site q+1, the bond split keeping chi_max singular values
  * (Fig. 3b), and site q+1's Kraus leg truncated to kappa_max.  The centre ends on q+1. */
 mpdo_status apply_2q(mpdo_t h, int q, const double* U, mpdo_chan_t ch);
+/* Noisy three-qubit gate on (q, q+1, q+2) (U host, 8x8 complex, qubit q most significant), for a
+ * three-qubit channel such as the crosstalk channel a tomography of a two-qubit gate together with its
+ * neighbour yields (Fig. 13b; up to 64 Kraus operators).  The centre is moved onto q, the three sites
+ * merged, the gate and channel applied with the new Kraus leg on site q+2, the bonds (q, q+1) and
+ * (q+1, q+2) split in turn keeping chi_max values each (Fig. 3b), and site q+2's Kraus leg truncated to
+ * kappa_max.  The centre ends on q+2.  The first call allocates the update's workspace (about
+ * 1536 chi_max^2 kappa_max^2 elements per chain; MPDO_ENOMEM if it does not fit, MPDO_ESTATE inside a
+ * capture).  Its eigenproblems are of order up to 2 chi_max kappa_max and 64 kappa_max, so the handle
+ * needs 2 chi_max kappa_max <= 512 and kappa_max <= 8 (MPDO_EINVAL otherwise). */
+mpdo_status apply_3q(mpdo_t h, int q, const double* U, mpdo_chan_t ch);
 /* Batched forms: U_dev = device array of batch gate matrices (complex128, row-major), chan_idx_dev =
  * device int[batch] choosing each chain's channel in ch (NULL: chain b uses channel b, or channel 0
  * for a one-channel set).  Both pointers are read when the work runs (capturable). */
 mpdo_status apply_1q_batch(mpdo_t h, int q, const double* U_dev, mpdo_chan_t ch, const int* chan_idx_dev);
 mpdo_status apply_2q_batch(mpdo_t h, int q, const double* U_dev, mpdo_chan_t ch, const int* chan_idx_dev);
+mpdo_status apply_3q_batch(mpdo_t h, int q, const double* U_dev, mpdo_chan_t ch, const int* chan_idx_dev);
 /* Truncate qubit q's Kraus leg to kappa (<= 0: kappa_max), Eq. svdNoise.  discarded (host, nullable)
  * receives batch relative discarded weights (synchronises when non-NULL). */
 mpdo_status truncate_kraus(mpdo_t h, int q, int kappa, double* discarded);
@@ -194,8 +207,11 @@ mpdo_status mpdo_set_purity_memory(mpdo_t h, long long bytes);
  *   4  the Kraus-leg Gram G = conj(X) X^T of every kappa truncation (GEMM)
  *   5  the product X = Y A2 of a two-qubit update, the gate and channel applied to the right site (GEMM)
  *   6  the bond eigensolver of a two-qubit update (top chi of F')
- *   7  the Kraus-leg eigensolver of every kappa truncation (top kappa of G) */
-#define MPDO_PROFILE_CLASSES 8
+ *   7  the Kraus-leg eigensolver of every kappa truncation (top kappa of G)
+ *   8  the two site-streaming products of every one-qubit update (the site's bond Gram and the
+ *      product with the folded gate); HBM-bound, so its second array entry holds the algorithmic
+ *      bytes (the site read twice, the new site written once) instead of flops */
+#define MPDO_PROFILE_CLASSES 9
 mpdo_status mpdo_profile(mpdo_t h, int enable);
 mpdo_status mpdo_profile_read(mpdo_t h, double* ms, double* flops, long long* count);
 
@@ -244,7 +260,8 @@ mpdo_status mpdo_wait_selftest(int limit_us, int* status_out);
 /* ---- Batched runtime: many independent noisy circuits ("instances") on one GPU.  The paper runs one
  * circuit at a time; this is the throughput form of the same per-gate update (Sec. II.C-II.D).
  * Instance c has n_qubits[c] qubits (starting in |0..0>) and the ops op_begin[c] .. op_begin[c+1]-1:
- *   op_kind[o]  1 or 2 (the gate acts on op_q[o], or on op_q[o] and op_q[o]+1), or
+ *   op_kind[o]  1 or 2 (the gate acts on op_q[o], or on op_q[o] and op_q[o]+1; three-qubit gates
+ *               are not taken by the batched runtime: use apply_3q_batch on a handle), or
  *               MPDO_OP_TRUNCATE_BONDS: the global bond truncation truncate_bonds(h, op_q[o], NULL)
  *               (1 <= op_q[o] <= chi_max; op_U and op_chi of the op are not read)
  *   op_U[o]     32 doubles: the 2x2 or 4x4 gate, complex row-major (interleaved re, im), 2x2 in the

@@ -70,6 +70,9 @@ class BatchedRun:
                     chi_of.append(0)
                     Us.append(np.zeros(16, dtype=np.complex128))
                     continue
+                if op.kind not in (1, 2):
+                    raise ValueError("the batched runtime takes one- and two-qubit gates (apply_3q_batch on a "
+                                     "handle takes three-qubit gates)")
                 nq, chi = c.chis[op.chan]
                 key = id(chi)
                 if key not in index:

@@ -85,25 +85,27 @@ struct EngBase {
   int snap_centre = 0;
   // optional per-launch CUDA-event timing by kernel class (not while capturing)
   enum { P_GEMM = 0, P_QR = 1, P_EIG = 2, P_OTHER = 3, P_GEMM_GRAM = 4, P_GEMM_X = 5, P_EIG_BOND = 6,
-         P_EIG_KRAUS = 7, P_N = 8 };
+         P_EIG_KRAUS = 7, P_ONEQ = 8, P_N = 9 };
   int prof_sub = -1;  // sub-class (one call site) of the next profiled launch, -1 = none
   bool prof_on = false;
   std::vector<cudaEvent_t> ev_pool;
   struct Rec {
     int cls, sub;
     int e0, e1;
-    double flops;
+    double flops, bytes;
   };
   std::vector<Rec> recs;
   int ev_next = 0;
   int cur_cls = -1, cur_sub = -1, cur_e0 = -1;
-  double cur_flops = 0;
+  double cur_flops = 0, cur_bytes = 0;
+  double prof_bytes = 0;  // algorithmic bytes of the next profiled launch (HBM-bound call sites)
   void prof_start(int cls, double flops) {
     if (!prof_on || capturing) return;
     if (ev_next + 2 > (int)ev_pool.size()) return;
     cur_cls = cls;
     cur_sub = prof_sub;
     cur_flops = flops;
+    cur_bytes = prof_bytes;
     cur_e0 = ev_next++;
     cudaEventRecord(ev_pool[cur_e0], stream);
   }
@@ -111,7 +113,7 @@ struct EngBase {
     if (cur_cls < 0) return;
     int e1 = ev_next++;
     cudaEventRecord(ev_pool[e1], stream);
-    recs.push_back({cur_cls, cur_sub, cur_e0, e1, cur_flops});
+    recs.push_back({cur_cls, cur_sub, cur_e0, e1, cur_flops, cur_bytes});
     cur_cls = -1;
   }
 
@@ -198,6 +200,11 @@ struct Eng : EngBase {
   int64_t sSK = 0;
   C* wHk = nullptr;  // Kraus-first update: the Gram H of Theta0 over (x, r), then the folded gate W
   int64_t sHk = 0;
+  // three-site update: allocated at the first three-qubit gate of the handle
+  C *w3a = nullptr, *w3b = nullptr, *w3c = nullptr, *w3K = nullptr, *w3F = nullptr, *w3U = nullptr;
+  CE *w3F64 = nullptr, *w3U64 = nullptr;
+  ER *w3Eval = nullptr, *w3Scr = nullptr;
+  int64_t s3a = 0, s3b = 0, s3c = 0, s3F = 0, s3Eval = 0, s3Scr = 0;
   // complex64: split operand planes of the tensor-core GEMM (floats, all chains); a product whose
   // planes do not fit runs on the CUDA cores
   float *tcA = nullptr, *tcB = nullptr;
@@ -214,7 +221,8 @@ struct Eng : EngBase {
 
   ~Eng() override {
     void* ptrs[] = {pool, wQR, wQ, wE, wT, wZ, wF, wU, wH, wY, wX, wK, wRt, wF64, wU64, wEval, wScr, dDisc, wSK,
-                    envL, envR, tmpA, tmpB, dDot, pX, pP, pE, pE2, iota, dStatus, wHk, tcA, tcB};
+                    envL, envR, tmpA, tmpB, dDot, pX, pP, pE, pE2, iota, dStatus, wHk, tcA, tcB,
+                    w3a, w3b, w3c, w3K, w3F, w3U, w3F64, w3U64, w3Eval, w3Scr};
     for (void* p : ptrs)
       if (p) cudaFree(p);
   }
@@ -449,29 +457,41 @@ struct Eng : EngBase {
   }
 
   // top-k eigenpairs of the column-major Hermitian matrices in wF (n x n), vectors to wU (col-major n x k)
-  mpdo_status eig_(int nmat, int k, int which /*0 chi, 1 kappa, -1 none*/) {
+  // Buffers of one eigensolver call: Gram matrices in (F, stride sF), eigenvectors out in (U, sU),
+  // their FP64 copies in the complex64 modes, eigenvalues and scratch.
+  struct EigBufs {
+    C *F, *U;
+    int64_t sF, sU;
+    CE *F64, *U64;
+    ER *eval, *scr;
+    int64_t sEval, sScr;
+  };
+  EigBufs main_bufs() { return {wF, wU, sF, sU, wF64, wU64, wEval, wScr, sEval, sScr}; }
+
+  mpdo_status eig_(int nmat, int k, int which /*0 chi, 1 kappa, -1 none*/, const EigBufs* eb = nullptr) {
     prof_sub = which == 0 ? P_EIG_BOND : which == 1 ? P_EIG_KRAUS : -1;
-    mpdo_status st = eig_impl(nmat, k, which);
+    const EigBufs b = eb ? *eb : main_bufs();
+    mpdo_status st = eig_impl(nmat, k, which, b);
     prof_sub = -1;
     return st;
   }
-  mpdo_status eig_impl(int nmat, int k, int which) {
+  mpdo_status eig_impl(int nmat, int k, int which, const EigBufs& b) {
+    EigArgs<ER> a;
+    a.n = nmat;
+    a.k = k;
+    a.astride = b.sF;
+    a.w = b.eval;
+    a.wstride = b.sEval;
+    a.vv = col_major(nmat, b.sU);
+    a.scratch = b.scr;
+    a.sstride = b.sScr;
+    a.disc = which >= 0 ? dDisc + which : nullptr;
+    a.gap = which >= 0 ? dDisc + 2 : nullptr;
+    a.disc_stride = 3;
+    a.status = dStatus;
     if (std::is_same<R, ER>::value) {
-      EigArgs<ER> a;
-      a.A = reinterpret_cast<CE*>(wF);
-      a.astride = sF;
-      a.n = nmat;
-      a.k = k;
-      a.w = wEval;
-      a.wstride = sEval;
-      a.V = reinterpret_cast<CE*>(wU);
-      a.vv = col_major(nmat, sU);
-      a.scratch = wScr;
-      a.sstride = sScr;
-      a.disc = which >= 0 ? dDisc + which : nullptr;
-      a.gap = which >= 0 ? dDisc + 2 : nullptr;
-      a.disc_stride = 3;
-      a.status = dStatus;
+      a.A = reinterpret_cast<CE*>(b.F);
+      a.V = reinterpret_cast<CE*>(b.U);
       prof_start(P_EIG, eig_flops(nmat, k) * B);
       CK(heevk<ER>(stream, B, a));
       prof_stop();
@@ -481,30 +501,17 @@ struct Eng : EngBase {
       const int sub = prof_sub;
       prof_sub = -1;
       prof_start(P_OTHER, 0);
-      CK((convert<R, ER>(stream, sF * B, wF, wF64)));
+      CK((convert<R, ER>(stream, b.sF * B, b.F, b.F64)));
       prof_stop();
       prof_sub = sub;
-      EigArgs<ER> a;
-      a.A = wF64;
-      a.astride = sF;
-      a.n = nmat;
-      a.k = k;
-      a.w = wEval;
-      a.wstride = sEval;
-      a.V = wU64;
-      a.vv = col_major(nmat, sU);
-      a.scratch = wScr;
-      a.sstride = sScr;
-      a.disc = which >= 0 ? dDisc + which : nullptr;
-      a.gap = which >= 0 ? dDisc + 2 : nullptr;
-      a.disc_stride = 3;
-      a.status = dStatus;
+      a.A = b.F64;
+      a.V = b.U64;
       prof_start(P_EIG, eig_flops(nmat, k) * B);
       CK(heevk<ER>(stream, B, a));
       prof_stop();
       prof_sub = -1;
       prof_start(P_OTHER, 0);
-      CK((convert<ER, R>(stream, sU * B, wU64, wU)));
+      CK((convert<ER, R>(stream, b.sU * B, b.U64, b.U)));
       prof_stop();
       prof_sub = sub;
       launches += 3;
@@ -613,7 +620,7 @@ struct Eng : EngBase {
     f.kraus = ch->kraus;
     f.chan_stride = (int64_t)ch->rpad * d * d;
     f.chan_idx = idx_dev;
-    f.Khat = wK;
+    f.Khat = nq == 3 ? w3K : wK;
     f.Rt = nq == 2 ? wRt : nullptr;
     // idx_dev == nullptr: one channel for all, or channel b for chain b (handled by chan_idx below)
     prof_start(P_OTHER, 0);
@@ -627,22 +634,27 @@ struct Eng : EngBase {
   // [l][p][nu][r] with S = dl*2 rows (l, p).  Eq. (svdNoise) through the Gram matrix X^* X^T.
   // With Yg (same layout as X, stride sY) the Gram is conj(X) Yg^T: Yg carries the environment of a
   // site next to the centre.
-  mpdo_status kappa_truncate_X(int NK, int S, int dr, int kap, int out_slot, const C* Yg = nullptr) {
+  // The three-site update passes its own X buffer (Xs, stride xs) and eigensolver buffers (eb).
+  mpdo_status kappa_truncate_X(int NK, int S, int dr, int kap, int out_slot, const C* Yg = nullptr,
+                               const C* Xs = nullptr, int64_t xs = 0, const EigBufs* eb = nullptr) {
     const int64_t L = (int64_t)S * dr;
+    const C* Xb = Xs ? Xs : wX;
+    const int64_t sx = Xs ? xs : sX;
+    const EigBufs b = eb ? *eb : main_bufs();
     // G = conj(X) X^T  (NK x NK, column-major, Hermitian: lower triangle computed, upper mirrored)
     prof_sub = P_GEMM_GRAM;
-    mpdo_status st = gemm_(NK, NK, (int)L, wX, v2(sX, 0, 0, L, 0, 0, 1, 1), Yg ? Yg : wX,
-                           v2(Yg ? sY : sX, 0, 0, 1, 0, 0, L, 0), wF, col_major(NK, sF), -1, 1);
+    mpdo_status st = gemm_(NK, NK, (int)L, Xb, v2(sx, 0, 0, L, 0, 0, 1, 1), Yg ? Yg : Xb,
+                           v2(Yg ? sY : sx, 0, 0, 1, 0, 0, L, 0), b.F, col_major(NK, b.sF), -1, 1);
     prof_sub = -1;
     if (st) return st;
     prof_start(P_OTHER, 0);
-    CK(herm_fill_upper<R>(stream, B, NK, wF, sF));
+    CK(herm_fill_upper<R>(stream, B, NK, b.F, b.sF));
     prof_stop();
     ++launches;
-    st = eig_(NK, kap, 1);
+    st = eig_(NK, kap, 1, &b);
     if (st) return st;
     // A[(s, nu, r)] = sum_nk V[nk, nu] X[nk][s][r]
-    return gemm_(kap, (int)L, NK, wU, v2(sU, 0, 0, NK, 0, 0, 1), wX, row_major(L, sX), slot_ptr(out_slot),
+    return gemm_(kap, (int)L, NK, b.U, v2(b.sU, 0, 0, NK, 0, 0, 1), Xb, row_major(L, sx), slot_ptr(out_slot),
                  v2(slot_elems, 0, 0, dr, dr, (int64_t)kap * dr, 1));
   }
 
@@ -650,16 +662,21 @@ struct Eng : EngBase {
   mpdo_status apply(int nq, int q, const double* Uhost, const double* Udev, const mpdo_chanset* ch,
                     const int* idx_dev) override {
     if (q < 0 || q + nq > n) return MPDO_EINVAL;
-    if (!ch || ch->nq != nq || ch->rpad > RMAX) return MPDO_EINVAL;
+    if (!ch || ch->nq != nq || ch->rpad > (nq == 3 ? 64 : RMAX)) return MPDO_EINVAL;
     if (!idx_dev && ch->count != 1 && ch->count != B) return MPDO_EINVAL;
     // a two-site split needs the centre on q or q + 1 (canonical environments on both sides); the other
     // site of the pair may be the non-isometric neighbour
     bool env = false;
     mpdo_status st = MPDO_OK;
-    if (nq == 2) {
+    if (nq == 3) {
+      st = check3(q, ch->rpad);
+      if (!st) st = move_centre(q);
+    } else if (nq == 2) {
       bool in_pair = (centre == q || centre == q + 1) && (dirty < 0 || dirty == q || dirty == q + 1);
       if (!in_pair) st = move_centre(q);
-    } else if (centre != q) {
+    } else if (centre != q || dirty >= 0) {
+      // a 1q truncation needs every other site isometric: with the centre on q a non-isometric
+      // neighbour is absorbed first (move_centre hops onto it and back)
       env = neighbour_trunc && (q == centre + 1 || q == centre - 1) && (dirty < 0 || dirty == q);
       if (!env) st = move_centre(q);
     }
@@ -669,6 +686,11 @@ struct Eng : EngBase {
     if (!idx && ch->count == B && B > 1) idx = iota;
     st = fuse_(nq, Uhost, Udev, ch, idx);
     if (st) return st;
+    if (nq == 3) {
+      st = apply3(q, ch->rpad);
+      dirty = -1;
+      return st;
+    }
     if (nq == 2) {
       st = trunc_order == MPDO_TRUNC_KRAUS_FIRST ? apply2_kraus_first(q, ch->rpad) : apply2(q, ch->rpad);
       dirty = -1;
@@ -689,10 +711,13 @@ struct Eng : EngBase {
     const int dl = bond[q], dn = kraus[q], dr = bond[q + 1];
     const int NK = rk * dn, NH = 2 * dn;
     const int64_t ld = (int64_t)2 * dn * dr;  // stride of l in a site
-    prof_sub = P_GEMM_GRAM;
+    const double site_bytes = (double)sizeof(C) * dl * ld * B;
+    prof_sub = P_ONEQ;
+    prof_bytes = site_bytes;  // the site streamed once (algorithmically)
     mpdo_status st = gemm_(NH, NH, dl * dr, site_ptr(q), v2(slot_elems, 0, 0, dr, dr, ld, 1, 1), Benv,
                            v2(bstride, dr, ld, 1, 0, 0, dr), wHk, row_major(NH, sHk));
     prof_sub = -1;
+    prof_bytes = 0;
     if (st) return st;
     prof_start(P_OTHER, 8.0 * NK * NK * 12 * B);
     CK(kraus_gram<R>(stream, B, 2, rk, dn, wK, wHk, sHk, wF, sF));
@@ -708,8 +733,12 @@ struct Eng : EngBase {
     ++launches;
     // A''[l][(p', nu)][r] = sum_{(p, n)} W[(p', nu), (p, n)] A[l][(p, n)][r]
     const int so = take_slot();
+    prof_sub = P_ONEQ;
+    prof_bytes = site_bytes * (1.0 + (double)kap / dn);  // the site read again, the new site written
     st = gemm_(2 * kap, dl * dr, NH, wHk, row_major(NH, sHk), site_ptr(q), v2(slot_elems, 0, 0, dr, dr, ld, 1),
                slot_ptr(so), v2(slot_elems, 0, 0, dr, dr, (int64_t)2 * kap * dr, 1));
+    prof_sub = -1;
+    prof_bytes = 0;
     if (st) return st;
     give_slot(site_slot[q]);
     site_slot[q] = so;
@@ -932,6 +961,163 @@ struct Eng : EngBase {
     bond[q + 1] = kchi;
     kraus[q + 1] = kap;
     centre = q + 1;
+    return MPDO_OK;
+  }
+
+  // ---------------------------------------------------------------- three-site update
+  // Workspace of the three-site update, sized from the caps at the first three-qubit gate: the
+  // merged tensor with the new Kraus leg is up to 2x * 2dn2 * rk * dn3 * 2dr <= 1024 chi^2 kappa^2
+  // elements per chain (x <= 2 chi, rk <= 64).
+  mpdo_status alloc3() {
+    if (w3a) return MPDO_OK;
+    if (capturing) return MPDO_ESTATE;
+    const int64_t X = chi_max, K = kappa_max;
+    const int n3 = (int)lmax(2 * X * K, 64 * K);  // <= 512 (check3)
+    s3a = 512 * K * K * X * X;
+    s3b = lmax(16 * K * K * X * X, 128 * K * X * X);
+    s3c = 1024 * K * K * X * X;
+    s3F = (int64_t)n3 * n3;
+    s3Eval = n3 + 1;
+    s3Scr = eig_scratch_elems(n3, n3);
+    bool ok = dmalloc(&w3a, s3a * B) == cudaSuccess && dmalloc(&w3b, s3b * B) == cudaSuccess &&
+              dmalloc(&w3c, s3c * B) == cudaSuccess && dmalloc(&w3K, (int64_t)64 * 64 * B) == cudaSuccess &&
+              dmalloc(&w3F, s3F * B) == cudaSuccess && dmalloc(&w3U, s3F * B) == cudaSuccess &&
+              dmalloc(&w3Eval, s3Eval * B) == cudaSuccess && dmalloc(&w3Scr, s3Scr * B) == cudaSuccess;
+    if (ok && !std::is_same<R, ER>::value)
+      ok = dmalloc(&w3F64, s3F * B) == cudaSuccess && dmalloc(&w3U64, s3F * B) == cudaSuccess;
+    if (!ok) {
+      void* ptrs[] = {w3a, w3b, w3c, w3K, w3F, w3U, w3F64, w3U64, w3Eval, w3Scr};
+      for (void* p : ptrs)
+        if (p) cudaFree(p);
+      w3a = w3b = w3c = w3K = w3F = w3U = nullptr;
+      w3F64 = w3U64 = nullptr;
+      w3Eval = w3Scr = nullptr;
+      cudaGetLastError();
+      return MPDO_ENOMEM;
+    }
+    return MPDO_OK;
+  }
+  // The shapes of a three-site update on (q, q+1, q+2) must fit the eigensolver (order <= 512) and
+  // the workspace; checked before anything is launched.
+  mpdo_status check3(int q, int rk) {
+    if (q < 0 || q + 3 > n || rk < 1 || rk > 64) return MPDO_EINVAL;
+    if (2 * chi_max * kappa_max > 512 || 64 * kappa_max > 512) return MPDO_EINVAL;
+    mpdo_status st = alloc3();
+    if (st) return st;
+    const int dl = bond[q], d1 = bond[q + 1], d2 = bond[q + 2], dr = bond[q + 3];
+    const int dn1 = kraus[q], dn2 = kraus[q + 1], dn3 = kraus[q + 2];
+    const int x = imin(dl * dn1, 2 * d1);
+    const int64_t C1 = (int64_t)4 * dn2 * rk * dn3 * dr;
+    const int k1 = (int)std::min<int64_t>(chi_max, std::min<int64_t>(2 * x, C1));
+    const int M2 = 2 * k1 * dn2, NK = rk * dn3;
+    const int64_t Cc = (int64_t)rk * dn3 * 2 * dr;
+    const int k2 = (int)std::min<int64_t>(chi_max, std::min<int64_t>(M2, Cc));
+    if (2 * x > 512 || M2 > 512 || NK > 512) return MPDO_EINVAL;
+    if ((int64_t)2 * x * 2 * dn2 * d2 > s3a || (int64_t)k1 * C1 > s3a || (int64_t)4 * x * dn2 * 2 * dn3 * dr > s3b ||
+        (int64_t)NK * 2 * k2 * dr > s3b || (int64_t)2 * x * C1 > s3c || (int64_t)M2 * M2 > s3F ||
+        (int64_t)NK * NK > s3F || (int64_t)4 * x * x > sF)
+      return MPDO_EINVAL;
+    return MPDO_OK;
+  }
+  // Noisy three-qubit channel on (q, q+1, q+2), e.g. the crosstalk channel from a tomography of a
+  // two-qubit gate with its neighbour (Fig. 13b), with the new Kraus leg on site q+2 and the centre on
+  // q: the pair reduced by the QR of A1 (Q1 R1), Theta0 = R1 A2 A3, the gate applied (gate3), the bond
+  // (q, q+1) split by the top-chi eigenvectors U1 of F1 = Theta Theta^H over (x, p1'), the rest
+  // R = U1^H Theta split at (q+1, q+2) by the top-chi eigenvectors U2 of F2 = R R^H over (b1, p2', n2),
+  // and site q+2's Kraus leg truncated (Eq. svdNoise).  The centre ends on q + 2.
+  mpdo_status apply3(int q, int rk) {
+    const int dl = bond[q], d1 = bond[q + 1], d2 = bond[q + 2], dr = bond[q + 3];
+    const int dn1 = kraus[q], dn2 = kraus[q + 1], dn3 = kraus[q + 2];
+    const int C2 = 2 * d1, m = dl * dn1, x = imin(m, C2);
+    // 1. QR of A1 as ((l, n1), (p1, b)) -> Q1 (m x x, wQ), R1 (x x 2 d1, wQR), column-major ld m
+    QrArgs<R> qa;
+    qa.m = m;
+    qa.n = C2;
+    qa.in = site_ptr(q);
+    qa.vin = v2(slot_elems, dn1, (int64_t)2 * dn1 * d1, d1, d1, (int64_t)dn1 * d1, 1);
+    qa.W = wQR;
+    qa.wstride = sQR;
+    qa.Qw = wQ;
+    qa.qstride = sQR;
+    qa.qout = nullptr;
+    prof_start(P_QR, qr_flops(qa.m, qa.n) * B);
+    CK(qr<R>(stream, B, qa));
+    prof_stop();
+    ++launches;
+    // 2. T12[(x, p1)][(p2, n2, b2)] = sum_b R1[x, (p1, b)] A2[b][(p2, n2, b2)]  (w3a)
+    const int N12 = 2 * dn2 * d2;
+    mpdo_status st = gemm_(2 * x, N12, d1, wQR, v2(sQR, 2, 1, (int64_t)d1 * m, 0, 0, m), site_ptr(q + 1),
+                           row_major(N12, slot_elems), w3a, row_major(N12, s3a));
+    if (st) return st;
+    // 3. Theta0[(x, p1, p2, n2)][(p3, n3, r)] = sum_b2 T12[(x, p1, p2, n2), b2] A3[b2][(p3, n3, r)]  (w3b)
+    const int N3 = 2 * dn3 * dr;
+    st = gemm_(4 * x * dn2, N3, d2, w3a, row_major(d2, s3a), site_ptr(q + 2), row_major(N3, slot_elems), w3b,
+               row_major(N3, s3b));
+    if (st) return st;
+    // 4. Theta[(x, p1')][(p2', n2, k, n3, p3', r)]  (w3c)
+    const int64_t C1 = (int64_t)4 * dn2 * rk * dn3 * dr;
+    prof_start(P_OTHER, 8.0 * 8 * 2 * x * C1 * B);
+    CK(gate3<R>(stream, B, x, dn2, dn3, dr, rk, w3K, w3b, s3b, w3c, s3c));
+    prof_stop();
+    ++launches;
+    // 5. bond (q, q+1): F1 = Theta Theta^H over (x, p1') (wF, column-major), its top k1 eigenpairs
+    const int X2 = 2 * x;
+    st = gemm_(X2, X2, (int)C1, w3c, row_major(C1, s3c), w3c, v2(s3c, 0, 0, 1, 0, 0, C1, 1), wF, col_major(X2, sF),
+               -1, 1);
+    if (st) return st;
+    prof_start(P_OTHER, 0);
+    CK(herm_fill_upper<R>(stream, B, X2, wF, sF));
+    prof_stop();
+    ++launches;
+    const int k1 = (int)std::min<int64_t>(chi_max, std::min<int64_t>(X2, C1));
+    st = eig_(X2, k1, 0);
+    if (st) return st;
+    // 6. A1' [l][p1'][n1][b'] = sum_x Q1[(l, n1), x] U1[(x, p1'), b']
+    const int s1 = take_slot();
+    st = gemm_(m, 2 * k1, x, wQ, col_major(m, sQR), wU, v2(sU, 0, 0, 2, k1, 1, (int64_t)X2), slot_ptr(s1),
+               v2(slot_elems, dn1, (int64_t)2 * dn1 * k1, k1, k1, (int64_t)dn1 * k1, 1));
+    if (st) return st;
+    // 7. R[b1][(p2', n2, k, n3, p3', r)] = sum_i conj(U1[i, b1]) Theta[i][...]  (w3a)
+    st = gemm_(k1, (int)C1, X2, wU, v2(sU, 0, 0, X2, 0, 0, 1, 1), w3c, row_major(C1, s3c), w3a, row_major(C1, s3a));
+    if (st) return st;
+    // 8. bond (q+1, q+2): F2 = R R^H over (b1, p2', n2) (w3F), its top k2 eigenpairs U2 (w3U)
+    const int M2 = 2 * k1 * dn2;
+    const int64_t Cc = (int64_t)rk * dn3 * 2 * dr;
+    st = gemm_(M2, M2, (int)Cc, w3a, row_major(Cc, s3a), w3a, v2(s3a, 0, 0, 1, 0, 0, Cc, 1), w3F,
+               col_major(M2, s3F), -1, 1);
+    if (st) return st;
+    prof_start(P_OTHER, 0);
+    CK(herm_fill_upper<R>(stream, B, M2, w3F, s3F));
+    prof_stop();
+    ++launches;
+    const EigBufs b3 = {w3F, w3U, s3F, s3F, w3F64, w3U64, w3Eval, w3Scr, s3Eval, s3Scr};
+    const int k2 = (int)std::min<int64_t>(chi_max, std::min<int64_t>(M2, Cc));
+    st = eig_(M2, k2, 0, &b3);
+    if (st) return st;
+    // 9. A2' [b1][p2'][n2][b2] = U2[(b1, p2', n2), b2]
+    const int s2 = take_slot();
+    CK(copy_view<R>(stream, B, M2, k2, w3U, col_major(M2, s3F), slot_ptr(s2), row_major(k2, slot_elems)));
+    ++launches;
+    // 10. X[(k, n3)][(b2, p3')][r] = sum_i conj(U2[i, b2]) R[i][(k, n3, p3', r)]  (w3b, Kraus-major)
+    st = gemm_(k2, (int)Cc, M2, w3U, v2(s3F, 0, 0, M2, 0, 0, 1, 1), w3a, row_major(Cc, s3a), w3b,
+               v2(s3b, 0, 0, 2 * dr, 2 * dr, (int64_t)2 * k2 * dr, 1));
+    if (st) return st;
+    // 11. Kraus-leg truncation of site q+2
+    const int NK = rk * dn3;
+    const int kap = imin(kappa_max, imin(2 * k2 * dr, NK));
+    const int s3 = take_slot();
+    st = kappa_truncate_X(NK, 2 * k2, dr, kap, s3, nullptr, w3b, s3b, &b3);
+    if (st) return st;
+    give_slot(site_slot[q]);
+    give_slot(site_slot[q + 1]);
+    give_slot(site_slot[q + 2]);
+    site_slot[q] = s1;
+    site_slot[q + 1] = s2;
+    site_slot[q + 2] = s3;
+    bond[q + 1] = k1;
+    bond[q + 2] = k2;
+    kraus[q + 2] = kap;
+    centre = q + 2;
     return MPDO_OK;
   }
 
@@ -1565,7 +1751,7 @@ mpdo_status mpdo_sync(mpdo_t h) {
 
 mpdo_status channel_set_from_process_matrices(mpdo_t h, int nq, int count, const double* chi, double tol,
                                               mpdo_chan_t* out, int* n_kraus) {
-  if (!h || !out || !chi || count < 1 || (nq != 1 && nq != 2)) return MPDO_EINVAL;
+  if (!h || !out || !chi || count < 1 || nq < 1 || nq > 3) return MPDO_EINVAL;
   if (h->e->capturing) return MPDO_ESTATE;
   if (!(tol > 0)) tol = 1e-12;
   const int d = 1 << nq, d2 = d * d;
@@ -1725,6 +1911,14 @@ mpdo_status apply_1q(mpdo_t h, int q, const double* U, mpdo_chan_t ch) {
 mpdo_status apply_2q(mpdo_t h, int q, const double* U, mpdo_chan_t ch) {
   if (!h || !U) return MPDO_EINVAL;
   return h->e->apply(2, q, U, nullptr, ch, nullptr);
+}
+mpdo_status apply_3q(mpdo_t h, int q, const double* U, mpdo_chan_t ch) {
+  if (!h || !U) return MPDO_EINVAL;
+  return h->e->apply(3, q, U, nullptr, ch, nullptr);
+}
+mpdo_status apply_3q_batch(mpdo_t h, int q, const double* U_dev, mpdo_chan_t ch, const int* chan_idx_dev) {
+  if (!h || !U_dev) return MPDO_EINVAL;
+  return h->e->apply(3, q, nullptr, U_dev, ch, chan_idx_dev);
 }
 mpdo_status apply_1q_batch(mpdo_t h, int q, const double* U_dev, mpdo_chan_t ch, const int* chan_idx_dev) {
   if (!h || !U_dev) return MPDO_EINVAL;
@@ -2058,7 +2252,7 @@ mpdo_status mpdo_profile_read(mpdo_t h, double* ms, double* flops, long long* co
     count[r.cls] += 1;
     if (r.sub >= 0) {
       ms[r.sub] += t;
-      flops[r.sub] += r.flops;
+      flops[r.sub] += r.sub == EngBase::P_ONEQ ? r.bytes : r.flops;
       count[r.sub] += 1;
     }
   }

@@ -92,7 +92,7 @@ cudaError_t kraus_tp_error(cudaStream_t s, int count, int nq, int rmax, const cp
 template <typename R>
 struct FuseArgs {
   int nq, rk;                    // rk = padded Kraus count
-  cplx<double> U[16];            // used when Udev == nullptr
+  cplx<double> U[64];            // used when Udev == nullptr (d x d, d <= 8)
   const cplx<double>* Udev;      // per instance d x d (row-major), stride d*d
   const cplx<double>* kraus;     // channel set: [chan][rk][d][d]
   int64_t chan_stride;
@@ -102,6 +102,13 @@ struct FuseArgs {
 };
 template <typename R>
 cudaError_t fuse_gate(cudaStream_t s, int batch, const FuseArgs<R>& a);
+
+// Three-qubit gate on a merged three-site tensor (one thread per output element):
+//   T[x][p1'][p2'][n2][k][n3][p3'][r] = sum_{p1 p2 p3} Khat_k[(p1' p2' p3'), (p1 p2 p3)] T0[x][p1][p2][n2][p3][n3][r]
+// Khat per instance [rk][8][8]; T0 and T the instance strides t0stride, tstride.
+template <typename R>
+cudaError_t gate3(cudaStream_t s, int batch, int X, int dn2, int dn3, int dr, int rk, const cplx<R>* Khat,
+                  const cplx<R>* T0, int64_t t0stride, cplx<R>* T, int64_t tstride);
 
 // T[c][a][c'][b] = sum_{p2, q2} Rt[(a,b),(p1,p2),(q1,q2)] E[(bb,p2),(bb',q2)], c = p1*dm + bb
 template <typename R>

@@ -96,7 +96,7 @@ __global__ void fuse_kernel(FuseArgs<R> a) {
     int k = e / dd, i = (e % dd) / d, j = e % d;
     cplx<double> acc = mk<double>(0, 0);
     for (int t = 0; t < d; ++t) cfma(acc, N[k * dd + i * d + t], U[t * d + j]);
-    Kh[e] = acc;
+    if (a.nq == 2) Kh[e] = acc;  // the reduced superoperator below needs the 2q operators only
     a.Khat[(int64_t)z * a.rk * dd + e] = mk<R>((R)acc.x, (R)acc.y);
   }
   __syncthreads();
@@ -159,6 +159,41 @@ __global__ void build_Y_kernel(int kchi, int dm, int rk, const cplx<R>* Khat, co
       for (int p1 = 0; p1 < 2; ++p1)
         cfma(acc, K[k * 16 + (p1p * 2 + p2p) * 4 + (p1 * 2 + p2)], Hz[(int64_t)(bp * 2 + p1p) * C2 + (p1 * dm + bb)]);
     Yz[e] = acc;
+  }
+}
+
+template <typename R>
+__global__ void gate3_kernel(int X, int dn2, int dn3, int dr, int rk, const cplx<R>* Khat, const cplx<R>* T0,
+                             int64_t t0stride, cplx<R>* T, int64_t tstride) {
+  const int z = blockIdx.y;
+  const cplx<R>* K = Khat + (int64_t)z * rk * 64;
+  const cplx<R>* Tz0 = T0 + (int64_t)z * t0stride;
+  cplx<R>* Tz = T + (int64_t)z * tstride;
+  const int64_t total = (int64_t)X * 4 * dn2 * rk * dn3 * 2 * dr;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t t = e;
+    const int r = (int)(t % dr);
+    t /= dr;
+    const int a3 = (int)(t % 2);
+    t /= 2;
+    const int n3 = (int)(t % dn3);
+    t /= dn3;
+    const int k = (int)(t % rk);
+    t /= rk;
+    const int n2 = (int)(t % dn2);
+    t /= dn2;
+    const int a2 = (int)(t % 2);
+    t /= 2;
+    const int a1 = (int)(t % 2);
+    const int64_t x = t / 2;
+    const cplx<R>* Kk = K + k * 64 + (a1 * 4 + a2 * 2 + a3) * 8;
+    cplx<R> acc = mk<R>(0, 0);
+    for (int b = 0; b < 8; ++b) {
+      const int b1 = b >> 2, b2 = (b >> 1) & 1, b3 = b & 1;
+      const int64_t src = (((((x * 2 + b1) * 2 + b2) * dn2 + n2) * 2 + b3) * dn3 + n3) * dr + r;
+      cfma(acc, Kk[b], Tz0[src]);
+    }
+    Tz[e] = acc;
   }
 }
 
@@ -373,8 +408,18 @@ cudaError_t kraus_tp_error(cudaStream_t s, int count, int nq, int rmax, const cp
 template <typename R>
 cudaError_t fuse_gate(cudaStream_t s, int batch, const FuseArgs<R>& a) {
   if (batch <= 0) return cudaSuccess;
-  if (a.rk > 16 || a.nq < 1 || a.nq > 2) return cudaErrorInvalidValue;
+  if (a.nq < 1 || a.nq > 3 || a.rk < 1 || a.rk > (a.nq == 3 ? 64 : 16)) return cudaErrorInvalidValue;
   fuse_kernel<R><<<batch, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+template <typename R>
+cudaError_t gate3(cudaStream_t s, int batch, int X, int dn2, int dn3, int dr, int rk, const cplx<R>* Khat,
+                  const cplx<R>* T0, int64_t t0stride, cplx<R>* T, int64_t tstride) {
+  if (batch <= 0) return cudaSuccess;
+  if (rk < 1 || rk > 64) return cudaErrorInvalidValue;
+  const int64_t total = (int64_t)X * 4 * dn2 * rk * dn3 * 2 * dr;
+  dim3 grid(grid_for(total), batch);
+  gate3_kernel<R><<<grid, NT, 0, s>>>(X, dn2, dn3, dr, rk, Khat, T0, t0stride, T, tstride);
   return cudaGetLastError();
 }
 template <typename R>
@@ -482,6 +527,8 @@ cudaError_t permute(cudaStream_t s, int batch, int nd, const int* dims, const in
 
 #define INST(R)                                                                                                  \
   template cudaError_t fuse_gate<R>(cudaStream_t, int, const FuseArgs<R>&);                                      \
+  template cudaError_t gate3<R>(cudaStream_t, int, int, int, int, int, int, const cplx<R>*, const cplx<R>*,      \
+                                int64_t, cplx<R>*, int64_t);                                                     \
   template cudaError_t build_T<R>(cudaStream_t, int, int, const cplx<R>*, const cplx<R>*, int64_t, cplx<R>*,     \
                                   int64_t);                                                                      \
   template cudaError_t build_Y<R>(cudaStream_t, int, int, int, int, const cplx<R>*, const cplx<R>*, int64_t,     \

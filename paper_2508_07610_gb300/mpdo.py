@@ -51,6 +51,8 @@ def lib():
         "channel_free": [vp],
         "apply_1q": [vp, i32, dp, vp],
         "apply_2q": [vp, i32, dp, vp],
+        "apply_3q": [vp, i32, dp, vp],
+        "apply_3q_batch": [vp, i32, vp, vp, vp],
         "apply_1q_batch": [vp, i32, vp, vp, vp],
         "apply_2q_batch": [vp, i32, vp, vp, vp],
         "truncate_kraus": [vp, i32, i32, dp],
@@ -113,7 +115,7 @@ class ChannelSet:
 
     def kraus(self, idx: int) -> np.ndarray:
         d = 2 ** self.nq
-        out = np.zeros((16, d, d), dtype=np.complex128)
+        out = np.zeros((int(self.ranks.max()) if self.count else 1, d, d), dtype=np.complex128)  # r_pad = max rank
         r = C.c_int()
         _check(lib().channel_kraus(self.h, idx, out.ctypes.data_as(C.POINTER(C.c_double)), C.byref(r)),
                "channel_kraus")
@@ -187,12 +189,14 @@ class MPDO:
     def profile(self, enable: bool = True):
         _check(lib().mpdo_profile(self.h, 1 if enable else 0), "mpdo_profile")
 
-    PROFILE_CLASSES = ("gemm", "qr", "eig", "other", "gemm_gram", "gemm_theta", "eig_bond", "eig_kraus")
+    PROFILE_CLASSES = ("gemm", "qr", "eig", "other", "gemm_gram", "gemm_theta", "eig_bond", "eig_kraus",
+                       "one_qubit")
 
     def profile_read(self):
         """{class: (ms, flops, launches)}; gemm, qr, eig and other partition every launch, the last
-        four are single call sites inside them (Kraus-leg Gram, the gate+channel product on the right
-        site, the bond and the Kraus-leg eigensolvers)."""
+        five are single call sites inside them (Kraus-leg Gram, the gate+channel product on the right
+        site, the bond and the Kraus-leg eigensolvers, and the site-streaming products of the 1q
+        update, for which the second entry is algorithmic bytes)."""
         nc = len(self.PROFILE_CLASSES)
         ms, fl = np.zeros(nc), np.zeros(nc)
         cnt = np.zeros(nc, dtype=np.int64)
@@ -212,6 +216,10 @@ class MPDO:
     def apply_2q(self, q: int, U: np.ndarray, ch: ChannelSet):
         u, p = _cdata(U)
         _check(lib().apply_2q(self.h, q, p, ch.h), "apply_2q")
+
+    def apply_3q(self, q: int, U: np.ndarray, ch: ChannelSet):
+        u, p = _cdata(U)
+        _check(lib().apply_3q(self.h, q, p, ch.h), "apply_3q")
 
     def apply_1q_batch(self, q: int, U_dev_ptr: int, ch: ChannelSet, idx_dev_ptr: Optional[int] = None):
         _check(lib().apply_1q_batch(self.h, q, C.c_void_p(U_dev_ptr), ch.h, C.c_void_p(idx_dev_ptr)),
@@ -382,7 +390,7 @@ def run_circuit(circuit, chi_max: int, kappa_max: int, prec="fp64", stream: int 
         ch = chans.get(op.chan)
         if ch is None:
             ch = chans[op.chan] = st.channels(op.kind, [circuit.chis[op.chan][1]])
-        (st.apply_1q if op.kind == 1 else st.apply_2q)(op.q, op.U, ch)
+        (st.apply_1q, st.apply_2q, st.apply_3q)[op.kind - 1](op.q, op.U, ch)
     st._channels = chans
     return st
 
