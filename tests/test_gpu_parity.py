@@ -427,3 +427,113 @@ def test_spam_distribution_closed_form():
         bits = [(z >> (n - 1 - i)) & 1 for i in range(n)]
         ref = np.prod([p1 if b else 1 - p1 for b in bits])
         assert abs(st.probability(bits)[0] - ref) < 1e-12
+
+
+# ------------------------------------------------------------------ three-qubit channels (Fig. 13b)
+def _three_qubit_circuit(n, layers, rng):
+    """Random gates with physical noise: AD o DEP on 1q gates, DEP2 o ZZ on 2q gates, and the
+    three-qubit crosstalk channel on random three-qubit gates."""
+    chis = [(1, W.kraus_to_chi(W.compose(W.amplitude_damping(3e-3), W.depolarizing_1q(2e-3)))),
+            (2, W.kraus_to_chi(W.compose(W.depolarizing_2q(1e-2), W.unitary_channel(W.zz_phase(0.02))))),
+            (3, W.kraus_to_chi(W.crosstalk_3q(1e-2, 0.02, 0.05, 2e-3)))]
+    ops = []
+    for layer in range(layers):
+        ops += [W.Op(1, q, W.random_unitary(2, rng), 0) for q in range(n)]
+        ops += [W.Op(3, q, W.random_unitary(8, rng), 2) for q in range(layer % 3, n - 2, 3)]
+        ops += [W.Op(2, q, W.random_unitary(4, rng), 1) for q in range((layer + 1) % 2, n - 1, 4)]
+    return W.Circuit(n, ops, chis)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp32"])
+@pytest.mark.parametrize("n,layers,chi,kap,seed", [(5, 4, 8, 4, 0), (6, 4, 6, 3, 1)])
+def test_three_qubit_channels_match_oracle(prec, n, layers, chi, kap, seed):
+    circ = _three_qubit_circuit(n, layers, np.random.default_rng(1200 + seed))
+    st = G.run_circuit(circ, chi, kap, prec)
+    orc = OM.run_circuit(circ, chi, kap)
+    assert orc.discarded_chi > 1e-6 and orc.discarded_kappa > 1e-6
+    _check_state(st, orc, prec, n, label=f"three-qubit channels n={n} chi={chi} kappa={kap}")
+
+
+def test_three_qubit_channels_exact_when_caps_cover_ranks():
+    rng = np.random.default_rng(600)
+    circ = W.random_circuit(4, 8, rng, rank1=1, rank2=1, p3q=0.5, rank3=2)
+    assert sum(op.kind == 3 for op in circ.ops) >= 3
+    st = G.run_circuit(circ, 32, 8, "fp64")
+    rho = _oracle_from_gpu(st).dense()
+    assert np.max(np.abs(rho - OD.run_circuit(circ))) < 1e-12
+    assert np.max(np.abs(st.discarded()[0][:2])) < 1e-13
+
+
+def test_crosstalk_channel_on_cnot_layers():
+    """CNOT layers whose gates carry the three-qubit crosstalk channel onto their right neighbour."""
+    rng = np.random.default_rng(77)
+    n = 6
+    ops, chis = [], []
+    chis.append((1, W.kraus_to_chi(W.depolarizing_1q(1e-3))))
+    chis.append((3, W.kraus_to_chi(W.crosstalk_3q(1e-2, 0.02, 0.05, 2e-3))))
+    for layer in range(4):
+        for q in range(n):
+            ops.append(W.Op(1, q, W.ry(rng.uniform(-np.pi, np.pi)), 0))
+        for q in range(layer % 2, n - 2, 3):
+            ops.append(W.Op(3, q, np.kron(W.cnot(), np.eye(2)), 1))
+    circ = W.Circuit(n, ops, chis)
+    for prec in ("fp64", "mixed"):
+        st = G.run_circuit(circ, 8, 4, prec)
+        orc = OM.run_circuit(circ, 8, 4)
+        _check_state(st, orc, prec, n, label=f"crosstalk 3q {prec}")
+
+
+def test_three_qubit_update_rejects_large_caps():
+    st = G.MPDO(4, 64, 8)
+    ch = st.channels(3, [W.kraus_to_chi(W.crosstalk_3q(1e-2, 0.02, 0.05, 2e-3))])
+    with pytest.raises(G.MPDOError):
+        st.apply_3q(0, np.eye(8), ch)
+
+
+# ------------------------------------------------------------------ scale of the state
+@pytest.mark.parametrize("prec,scale", [("fp64", 1e-60), ("mixed", 1e-12), ("fp32", 1e-12)])
+def test_tiny_norm_state_truncates_like_a_unit_one(prec, scale):
+    """Nothing is renormalised, so after many lossy truncations the state's norm can be tiny.  The
+    truncations depend only on ratios: a state scaled by `scale` must give the same normalised readouts
+    and discarded weights as the unscaled oracle run, and its trace scaled by scale^2."""
+    rng = np.random.default_rng(1300)
+    circ = W.random_circuit(5, 20, rng, rank1=3, rank2=5)
+    st = G.MPDO(5, 4, 3, prec)
+    site = np.zeros((1, 2, 1, 1), dtype=np.complex128)
+    site[0, 0, 0, 0] = scale
+    st.set_site(0, site)
+    chans = {}
+    for op in circ.ops:
+        ch = chans.get(op.chan)
+        if ch is None:
+            ch = chans[op.chan] = st.channels(op.kind, [circ.chis[op.chan][1]])
+        (st.apply_1q if op.kind == 1 else st.apply_2q)(op.q, op.U, ch)
+    orc = OM.run_circuit(circ, 4, 3)
+    assert orc.discarded_chi > 1e-6 and orc.discarded_kappa > 1e-6
+    lim = readout_limit(orc, prec)
+    rho_g = _oracle_from_gpu(st).dense()
+    rho_o = orc.dense()
+    assert np.max(np.abs(rho_g / np.trace(rho_g) - rho_o / np.trace(rho_o))) < lim
+    assert np.max(np.abs(st.zz_map()[0] - orc.zz_map())) < lim
+    assert abs(st.trace()[0] / scale ** 2 - orc.trace()) < TRACE_TOL[prec] * orc.trace() + allowance(orc, prec)
+    disc = st.discarded()[0]
+    assert abs(disc[0] - orc.discarded_chi) < discarded_limit(orc, prec, "chi")
+    assert abs(disc[1] - orc.discarded_kappa) < discarded_limit(orc, prec, "kappa")
+
+
+def test_deep_lossy_qaoa_instance_stays_finite():
+    """A 24-qubit p = 4 QAOA instance whose truncations discard about 3 % per update: its norm decays
+    to about 1e-18, which once put the eigensolvers' absolute safeguards out of scale."""
+    circs = W.qaoa_batch(4096, seed=W.MASTER_SEED + 3)
+    c = circs[3187]
+    assert c.n == 24 and len(c.ops) > 1000
+    traces = {}
+    for prec in ("mixed", "fp64"):
+        st = G.run_circuit(c, 32, 8, prec)
+        traces[prec] = st.trace()[0]
+        pos = {v: i for i, v in enumerate(c.meta["perm"])}
+        mc = st.maxcut([(pos[u], pos[v]) for u, v in c.meta["edges"]])[0]
+        assert np.isfinite(mc) and 0 <= mc <= len(c.meta["edges"])
+        disc = st.discarded()[0]
+        assert 0 < disc[0] < 2 * len(c.ops) and 0 < disc[1] < 2 * len(c.ops)
+    assert 0 < traces["fp64"] < 1e-6 and 0 < traces["mixed"] < 1e-6
