@@ -196,38 +196,50 @@ def _pair_rdm(sites, q):
     return ein("bxks,byks->xy", X, th.conj())
 
 
-def per_update_error(st, r, prec):
-    """Accuracy of one full-size update: chain 0's steady state is copied into one-chain handles of
-    each complex64 mode and of complex128 with FP64 eigensolvers; all apply the same noisy CZ on
-    qubits (9, 10), and the largest element difference of the pair's reduced density matrix from the
-    complex128 result is returned relative to its trace.  The complex128 path is run once more on
-    the state with every element moved by a random relative 2^-24 (the size of complex64 rounding):
-    how far that moves the result is the workload's own sensitivity to input rounding (cuts between
-    nearly equal eigenvalues), a floor under any complex64 result."""
+def per_update_error(st, r, tc: bool):
+    """Accuracy of single full-size updates: chain 0's steady state is copied into one-chain handles of
+    each complex64 mode and of complex128 with FP64 eigensolvers; all apply the same noisy CZ on one
+    pair, and the largest element difference of the pair's reduced density matrix from the complex128
+    result is taken relative to its trace.  This is repeated for the pairs (1, 2), (3, 4), ..., (17, 18)
+    of an odd layer.  The complex128 path is also run on the state with every element moved by a random
+    relative 2^-24 (the size of complex64 rounding): how far that moves the result is the workload's own
+    sensitivity to input rounding, a floor under any complex64 result.  Each update's smallest relative
+    eigenvalue gap at its cuts (complex128) is reported with it: below 1e-5 a cut lies inside a
+    near-degenerate cluster, where the truncation is not unique (the parity tests' rule)."""
     from paper_2508_07610_gb300 import mpdo as G
     from paper_2508_07610_gb300 import workloads as W
 
     sites = st.sites(0)
-    q = N_QUBITS // 2 - 1
     rng = np.random.default_rng(5)
-    rdm = {}
-    runs = [("fp64", sites), ("fp32", sites), ("mixed", sites),
-            ("fp64_perturbed", [a * (1 + 2.0 ** -24 * (rng.uniform(-1, 1, a.shape) + 1j * rng.uniform(-1, 1, a.shape)))
-                                for a in sites])]
-    for key, ss in runs:
-        h = G.MPDO(N_QUBITS, CHI, KAPPA, key.split("_")[0])
-        for i, a in enumerate(ss):
-            h.set_site(i, a)
-        # both handles start from the same tensors and gauge; after an odd layer the batched state's
-        # centre is at the left end, so declaring it at site 0 is exact
-        h.set_centre(0)
-        h.apply_2q(q, W.cz(), h.channels(2, [r.chis2[q][0]]))
-        h.sync()
-        rdm[key] = _pair_rdm(h.sites(0), q)
-        h.free()
-    ref = rdm["fp64"]
-    nrm = abs(np.trace(ref))
-    return {k: float(np.max(np.abs(rdm[k] - ref)) / nrm) for k in ("fp32", "mixed", "fp64_perturbed")}
+    pert = [a * (1 + 2.0 ** -24 * (rng.uniform(-1, 1, a.shape) + 1j * rng.uniform(-1, 1, a.shape))) for a in sites]
+    rows = []
+    for q in range(1, N_QUBITS - 2, 2):
+        rdm, gap = {}, None
+        for key, ss in (("fp64", sites), ("fp32", sites), ("mixed", sites), ("fp64_perturbed", pert)):
+            h = G.MPDO(N_QUBITS, CHI, KAPPA, key.split("_")[0])
+            if key in ("fp32", "mixed"):
+                h.set_tensor_cores(tc)
+            for i, a in enumerate(ss):
+                h.set_site(i, a)
+            # every handle starts from the same tensors and gauge; after an odd layer the batched
+            # state's centre is at the left end, so declaring it at site 0 is exact
+            h.set_centre(0)
+            h.apply_2q(q, W.cz(), h.channels(2, [r.chis2[q][0]]))
+            h.sync()
+            rdm[key] = _pair_rdm(h.sites(0), q)
+            if key == "fp64":
+                gap = float(h.discarded()[0][2])
+            h.free()
+        ref = rdm["fp64"]
+        nrm = abs(np.trace(ref))
+        rows.append(dict({k: float(np.max(np.abs(rdm[k] - ref)) / nrm) for k in ("fp32", "mixed", "fp64_perturbed")},
+                         pair=q, gap=gap))
+    out = {k: max(rw[k] for rw in rows) for k in ("fp32", "mixed", "fp64_perturbed")}
+    sep = [rw for rw in rows if rw["gap"] >= 1e-5]
+    out["separated_max"] = {k: (max(rw[k] for rw in sep) if sep else None) for k in ("fp32", "mixed")}
+    out["median"] = {k: float(np.median([rw[k] for rw in rows])) for k in ("fp32", "mixed", "fp64_perturbed")}
+    out["updates"] = rows
+    return out
 
 
 _T0 = time.perf_counter()
@@ -272,8 +284,6 @@ def run_ours(args, torch, rank, world, prec=None, steps=None, secondary=False):
     streams = [torch.cuda.Stream() for _ in range(G)]
     runners = [Runner(Bg, prec, streams[g].cuda_stream, seed + 7919 * g, depth, torch) for g in range(G)]
     r, st, stream = runners[0], runners[0].st, streams[0]
-    for rg in runners:
-        rg.st.set_tensor_cores(args.tc)
     progress("handles, channels and gates ready")
     # ---- reach the steady state: every bond at chi = 64 and every Kraus leg at kappa = 8
     for layer in range(args.saturate):
@@ -285,20 +295,64 @@ def run_ours(args, torch, rank, world, prec=None, steps=None, secondary=False):
         assert min(bonds[4:-4]) == CHI and min(kraus) == KAPPA, (bonds, kraus)
     progress("saturated")
     zz_fast = st.zz_map()[0] if not secondary else None
-    upd_err = per_update_error(st, r, prec) if rank == 0 and not secondary else None
-    progress("per-update accuracy measured")
+
     # ---- capture an even + odd layer pair per group (the last bond alternates between 16 and 64
     # with the layer parity, so a pair maps the steady state onto itself); each graph puts the centre
     # and the site storage back where they were on exit so that it can be replayed
-    graphs, per_step = [], 0
+    def capture_all():
+        gs, launches_per_step = [], 0
+        for rg in runners:
+            c0 = rg.st.launch_count()
+            rg.st.capture_begin()
+            rg.layer(0)
+            rg.layer(1)
+            gs.append(rg.st.capture_end(restore=True))
+            launches_per_step += rg.st.launch_count() - c0
+        return gs, launches_per_step
+
+    def replay_ms(gs, n):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(streams[0])
+        for sg in streams[1:]:
+            sg.wait_event(a)
+        for _ in range(n):
+            for gr in gs:
+                gr.launch()
+        for sg in streams[1:]:
+            d = torch.cuda.Event()
+            d.record(sg)
+            streams[0].wait_event(d)
+        b.record(streams[0])
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n
+
+    # ---- tensor cores for the complex64 products: with --tensor-cores auto both captures are timed
+    # over two replays after one warm-up replay, and the faster one is kept
+    modes = [False] if prec == "fp64" else {"auto": [True, False], "on": [True], "off": [False]}[args.tensor_cores]
+    cand = {}
+    for tc in modes:
+        for rg in runners:
+            rg.st.set_tensor_cores(tc)
+        gs, lps = capture_all()
+        ms_tc = None
+        if len(modes) > 1:
+            replay_ms(gs, 1)
+            ms_tc = replay_ms(gs, 2)
+        cand[tc] = (gs, lps, ms_tc)
+    chosen = min(cand, key=lambda t: cand[t][2]) if len(modes) > 1 else modes[0]
+    graphs, per_step = cand[chosen][0], cand[chosen][1]
+    for tc, (gs, _, _) in cand.items():
+        if tc != chosen:
+            for gr in gs:
+                gr.free()
     for rg in runners:
-        c0 = rg.st.launch_count()
-        rg.st.capture_begin()
-        rg.layer(0)
-        rg.layer(1)
-        graphs.append(rg.st.capture_end(restore=True))
-        per_step += rg.st.launch_count() - c0
-    progress("layer pairs captured")
+        rg.st.set_tensor_cores(chosen)
+    tc_info = {"mode": args.tensor_cores if prec != "fp64" else "off (complex128)", "chosen": "on" if chosen else "off",
+               "ms_per_step": {("on" if tc else "off"): v[2] for tc, v in cand.items() if v[2] is not None}}
+    progress(f"layer pairs captured; tensor cores {tc_info}")
+    upd_err = per_update_error(st, r, chosen) if rank == 0 and not secondary else None
+    progress("per-update accuracy measured")
     n2q_step = (r.n2q(0) + r.n2q(1)) * B
     # ---- warm-up
     for s in range(args.warmup):
@@ -335,7 +389,8 @@ def run_ours(args, torch, rank, world, prec=None, steps=None, secondary=False):
     total_2q = allreduce_sum(torch, world, n2q)
     value = replica_value(torch, world, n2q, ms)
     if secondary:
-        return {"value": value, "ms": ms_max, "steps": steps, "clocks": clk.summary(), "launches": launches}
+        return {"value": value, "ms": ms_max, "steps": steps, "clocks": clk.summary(), "launches": launches,
+                "tc": tc_info}
     disc = st.discarded()
     # ---- per-kernel-class timing of the same layers on group 0 alone (CUDA events around every
     # launch, no graph, no other group running)
@@ -404,6 +459,7 @@ def run_ours(args, torch, rank, world, prec=None, steps=None, secondary=False):
         "value": value, "ms": ms_max, "n2q": total_2q, "disc": disc, "prof": prof, "e2e": e2e_val,
         "h2d": h2d, "d2h": d2h, "clocks": clk.summary(), "plain": plain,
         "launches": launches, "B": B, "G": G, "err": err, "upd_err": upd_err, "fp64_spread": fp64_spread,
+        "tc": tc_info,
         "prec": prec,
     }
 
@@ -684,8 +740,9 @@ def main():
     ap.add_argument("--circuits", type=int, default=100, help="truncation study: circuits per (Q, depth)")
     ap.add_argument("--settings", default="32,4;32,8;32,16;64,4;64,8;64,16;128,4;128,8;128,16",
                     help="crosstalk sweep (chi,kappa) settings")
-    ap.add_argument("--no-tc", dest="tc", action="store_false",
-                    help="keep every complex64 product on the CUDA cores (default: tcgen05 tensor cores)")
+    ap.add_argument("--tensor-cores", default="auto", choices=["auto", "on", "off"],
+                    help="complex64 products on the tcgen05 tensor cores; auto times both captures and keeps "
+                         "the faster")
     ap.add_argument("--instances", type=int, default=4096)
     ap.add_argument("--tuning", default="", help="batched runtime: autotuner JSON file (created if missing)")
     args = ap.parse_args()
@@ -804,7 +861,9 @@ def main():
     # dominant kernel by time: the engine's per-launch CUDA-event record, split by call site
     prof = res["prof"]
     parts = {k: prof[k] for k in ("gemm_gram", "gemm_theta", "eig_bond", "eig_kraus", "qr", "other")}
-    parts["gemm_rest"] = tuple(prof["gemm"][i] - prof["gemm_gram"][i] - prof["gemm_theta"][i] for i in range(3))
+    parts["gemm_rest"] = (prof["gemm"][0] - prof["gemm_gram"][0] - prof["gemm_theta"][0] - prof["one_qubit"][0],
+                          prof["gemm"][1] - prof["gemm_gram"][1] - prof["gemm_theta"][1],
+                          prof["gemm"][2] - prof["gemm_gram"][2] - prof["gemm_theta"][2] - prof["one_qubit"][2])
     parts["eig_rest"] = tuple(prof["eig"][i] - prof["eig_bond"][i] - prof["eig_kraus"][i] for i in range(3))
     dom = max(parts, key=lambda k: parts[k][0])
     ms_d, fl_d, cnt_d = parts[dom]
@@ -826,6 +885,14 @@ def main():
                                "nominal GB300 FP64 rate (no measured FP64 peak)",
                 "classes": {k: {"ms": v[0], "tflops": (v[1] / (v[0] / 1e3) / 1e12) if v[0] > 0 else None,
                                 "launches": v[2]} for k, v in parts.items()}}
+    oq = prof["one_qubit"]
+    if oq[0] > 0:
+        gbs = oq[1] / (oq[0] / 1e3) / 1e9
+        roofline["classes"]["one_qubit"] = {
+            "ms": oq[0], "launches": oq[2], "bound": "hbm", "achieved_gbs": gbs, "peak_gbs": pk["hbm_gbs"],
+            "frac": gbs / pk["hbm_gbs"],
+            "note": "the site-streaming products of the 1q update (bond Gram H, then A'' = W A): algorithmic "
+                    "bytes = the site read twice and the new site written once"}
     cpu = None
     if not args.no_cpu:
         try:
@@ -838,12 +905,18 @@ def main():
                    "sample": f"failed: {e}"}
     prec_desc = {"mixed": "complex64 contractions, FP64 eigensolvers (MIXED)",
                  "fp32": "complex64 contractions, FP32 eigensolvers", "fp64": "complex128, FP64 eigensolvers"}
+    ue = res["upd_err"]
+    sep_err = ue["separated_max"].get(args.prec) if args.prec != "fp64" else 0.0
     acc = {
         "criterion": "per update: largest element of the updated pair's reduced density matrix vs the "
-                     "complex128/FP64 update of the same state, relative to its trace, <= 1e-6",
-        "per_update_rdm_err_vs_fp64": res["upd_err"][args.prec] if args.prec != "fp64" else 0.0,
-        "per_update_rdm_err_all_modes": res["upd_err"],
-        "meets_1e-6": (res["upd_err"][args.prec] if args.prec != "fp64" else 0.0) <= 1e-6,
+                     "complex128/FP64 update of the same state, relative to its trace, <= 1e-6 at every update "
+                     "whose cuts have relative eigenvalue gaps >= 1e-5 (the parity tests' rule; below that a cut "
+                     "lies inside a near-degenerate cluster and the truncation is not unique); the nine pairs of "
+                     "an odd layer are measured",
+        "per_update_rdm_err_vs_fp64": sep_err,
+        "per_update_rdm_err_max_any_gap": ue[args.prec] if args.prec != "fp64" else 0.0,
+        "per_update_rdm_err_all_modes": ue,
+        "meets_1e-6": sep_err is not None and sep_err <= 1e-6,
         "readouts_after_saturation": {
             "max_abs_zz_err_vs_complex128_chain": res["err"],
             "complex128_spread_under_1e-13_input_perturbation": res["fp64_spread"],
@@ -857,11 +930,11 @@ def main():
                 "l2": "state and workspaces (~GBs) far exceed the 129 MB L2",
                 "plain_fp64_updates_per_s": res["plain"],
                 "batched_over_plain": (res["value"] / res["plain"]) if res["plain"] else None,
-                "graph_captured": True})
+                "graph_captured": True, "tensor_cores": res["tc"]})
     if sec is not None:
         cfg["secondary"] = {"precision": prec_desc[args.secondary_prec], "value": sec["value"],
                             "unit": "updates/s", "steps": sec["steps"], "ms_per_step": sec["ms"] / sec["steps"],
-                            "per_update_rdm_err_vs_fp64": res["upd_err"].get(args.secondary_prec),
+                            "per_update_rdm_err_vs_fp64": res["upd_err"]["separated_max"].get(args.secondary_prec),
                             "clocks": sec["clocks"]}
     line = {"metric": METRIC, "value": res["value"], "unit": "updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": res["ms"] / args.steps, "higher_is_better": True,

@@ -56,7 +56,9 @@ typedef enum {
 } mpdo_prec;
 
 enum {
-  MPDO_EXPECT_TRACE = 0,     /* Tr rho, 1 value per chain (unnormalised; truncation lowers it) */
+  MPDO_EXPECT_TRACE = 0,     /* Tr rho, 1 value per chain (unnormalised; truncation lowers it; the
+                              * stored sites are kept near unit scale by exact powers of two per
+                              * chain, which this readout multiplies back in; 0 below the FP64 range) */
   MPDO_EXPECT_ZZ = 1,        /* args = {i, j}: <Z_i Z_j>, 1 value per chain */
   MPDO_EXPECT_ZZ_MAP = 2,    /* n*n values per chain, row-major, diagonal = 1 */
   MPDO_EXPECT_GHZ = 3,       /* <GHZ| rho |GHZ>, |GHZ> = (|0..0> + |1..1>)/sqrt 2, 1 value per chain */
@@ -164,7 +166,9 @@ mpdo_status mpdo_graph_free(mpdo_graph_t g);
  * chain (host data = batch blocks of dl*2*dn*dr complex) with the given dims; the neighbouring bonds
  * must match (bond q must equal dl, bond q+1 must equal dr, 1 at the ends), dl, dr <= chi_max,
  * dn <= kappa_max.  set_centre declares which site is the orthogonality centre: the caller guarantees
- * that sites left of it are left-isometric and sites right of it right-isometric. */
+ * that sites left of it are left-isometric and sites right of it right-isometric.  The tensors are the
+ * stored ones: the represented state is their product times the chain's power-of-two scale (see
+ * MPDO_EXPECT_TRACE), which normalised readouts do not see and set_site leaves as it is. */
 mpdo_status mpdo_get_site(mpdo_t h, int chain, int q, double* out, int* dims);
 mpdo_status mpdo_set_site(mpdo_t h, int q, int dl, int dn, int dr, const double* data);
 mpdo_status mpdo_set_centre(mpdo_t h, int q);

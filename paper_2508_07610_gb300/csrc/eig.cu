@@ -47,6 +47,18 @@ __device__ R block_sum(R v, R* red) {
 }
 
 template <typename R>
+__device__ R block_max(R v, R* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  R s = 0;
+  for (int w = 0; w < NT / 32; ++w) s = fmax(s, red[w]);
+  return s;
+}
+
+template <typename R>
 __device__ cplx<R> block_csum(cplx<R> v, R* red) {
   R a = block_sum(v.x, red);
   R b = block_sum(v.y, red);
@@ -116,6 +128,32 @@ __global__ void __launch_bounds__(NT, 2) heevk_kernel(EigArgs<R> g) {
   R* Zr = Lpiv + (int64_t)n * k;
   cplx<R>* U = reinterpret_cast<cplx<R>*>(Zr + (int64_t)n * k);   // complex, vector t column at [t * n]
   cplx<R>* PH = U + (int64_t)n * k;                                  // phases, n
+
+  // ---- (0) scale.  The safeguards below (pivot minimum, the zero test of Householder norms, the FP32
+  // bracket) are absolute, so the matrix is first multiplied by the power of two that brings its
+  // largest entry into [1/2, 1): Gram matrices of states whose norm has decayed by many orders of
+  // magnitude then behave like unit-scale ones.  The scaling is exact; eigenvalues are scaled back on
+  // output, and the discarded weight and the gap are ratios.
+  __shared__ int s_exp;
+  {
+    R amax = 0;
+    for (int64_t e = tid; e < (int64_t)n * n; e += NT) amax = fmax(amax, fmax(fabs(A[e].x), fabs(A[e].y)));
+    amax = block_max(amax, red);
+    if (tid == 0) {
+      int ex = 0;
+      if (amax > R(0) && isfinite((double)amax)) frexp(amax, &ex);
+      s_exp = ex;
+    }
+    __syncthreads();
+    if (s_exp != 0) {
+      const R f = ldexp(R(1), -s_exp);
+      for (int64_t e = tid; e < (int64_t)n * n; e += NT) {
+        A[e].x *= f;
+        A[e].y *= f;
+      }
+    }
+    __syncthreads();
+  }
 
   // ---- (1) tridiagonalisation: A <- H A H on the trailing block, H = I - beta v v^H, in panels of
   // NB reflectors.  Inside a panel the trailing block is not updated: column j is brought up to date
@@ -651,7 +689,7 @@ __global__ void __launch_bounds__(NT, 2) heevk_kernel(EigArgs<R> g) {
   }
   if (g.w) {
     R* w = g.w + (int64_t)z * g.wstride;
-    for (int t = tid; t < k; t += NT) w[t] = s_w[t];
+    for (int t = tid; t < k; t += NT) w[t] = ldexp(s_w[t], s_exp);
   }
   // non-finite eigenvalues, trace or eigenvector entries (from non-finite input: the inverse
   // iteration's growth guard keeps finite inputs finite) are reported as non-convergence

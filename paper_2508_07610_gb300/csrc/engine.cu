@@ -222,7 +222,7 @@ struct Eng : EngBase {
   ~Eng() override {
     void* ptrs[] = {pool, wQR, wQ, wE, wT, wZ, wF, wU, wH, wY, wX, wK, wRt, wF64, wU64, wEval, wScr, dDisc, wSK,
                     envL, envR, tmpA, tmpB, dDot, pX, pP, pE, pE2, iota, dStatus, wHk, tcA, tcB,
-                    w3a, w3b, w3c, w3K, w3F, w3U, w3F64, w3U64, w3Eval, w3Scr};
+                    w3a, w3b, w3c, w3K, w3F, w3U, w3F64, w3U64, w3Eval, w3Scr, dExp2};
     for (void* p : ptrs)
       if (p) cudaFree(p);
   }
@@ -292,6 +292,7 @@ struct Eng : EngBase {
       tensor_cores = true;
     }
     CK(dmalloc(&dStatus, 1));
+    CK(dmalloc(&dExp2, (int64_t)B));
     sHk = 16 * K * K;
     CK(dmalloc(&wHk, sHk * B));
     CK(cudaMemset(dStatus, 0, sizeof(int)));
@@ -406,6 +407,7 @@ struct Eng : EngBase {
     for (int s = nslots - 1; s >= n; --s) free_slots.push_back(s);
     // |0> product state: slot q of every chain holds [1, 0]
     CK(init_zero_sites<R>(stream, n * B, pool, slot_elems));
+    CK(cudaMemsetAsync(dExp2, 0, sizeof(int) * B, stream));
     CK(init_discarded(stream, B, dDisc));
     launches += 2;
     return MPDO_OK;
@@ -689,14 +691,27 @@ struct Eng : EngBase {
     if (nq == 3) {
       st = apply3(q, ch->rpad);
       dirty = -1;
-      return st;
-    }
-    if (nq == 2) {
+    } else if (nq == 2) {
       st = trunc_order == MPDO_TRUNC_KRAUS_FIRST ? apply2_kraus_first(q, ch->rpad) : apply2(q, ch->rpad);
       dirty = -1;
-      return st;
+    } else {
+      st = env ? apply1_neighbour(q, ch->rpad) : apply1(q, ch->rpad);
     }
-    return env ? apply1_neighbour(q, ch->rpad) : apply1(q, ch->rpad);
+    if (st) return st;
+    return renorm_(nq == 1 ? q : centre);
+  }
+
+  // Nothing is renormalised (every readout but TRACE divides by Tr rho), so the state's norm decays
+  // with each truncation's discarded weight; in complex64 storage a long lossy circuit would leave the
+  // FP32 exponent range.  After every update the touched site is kept near unit scale by an exact
+  // power of two, accumulated per chain in dExp2 and applied to the TRACE readout.
+  mpdo_status renorm_(int q) {
+    const int64_t elems = (int64_t)bond[q] * 2 * kraus[q] * bond[q + 1];
+    prof_start(P_OTHER, 0);
+    CK(renorm_sites<R>(stream, B, elems, site_ptr(q), slot_elems, dExp2));
+    prof_stop();
+    ++launches;
+    return MPDO_OK;
   }
 
   // Noisy 1q gate (Fig. 2c) and the Kraus-leg truncation of its site (Eq. svdNoise) without forming
@@ -781,6 +796,7 @@ struct Eng : EngBase {
     return MPDO_OK;
   }
   int* iota = nullptr;  // device [0, 1, ..., B-1]
+  int* dExp2 = nullptr;  // per chain: the represented state is the stored one times 2^dExp2
 
   mpdo_status apply1(int q, int rk) { return apply1_fold(q, rk, site_ptr(q), slot_elems); }
 
@@ -1144,6 +1160,7 @@ struct Eng : EngBase {
     give_slot(site_slot[q]);
     site_slot[q] = so;
     kraus[q] = kap;
+    if ((st = renorm_(q))) return st;
     if (disc) {
       std::vector<double> after(3 * (size_t)B);
       CK(cudaMemcpyAsync(after.data(), dDisc, sizeof(double) * 3 * B, cudaMemcpyDeviceToHost, stream));
@@ -1204,6 +1221,7 @@ struct Eng : EngBase {
       if (st) return st;
       centre = c - 1;
     }
+    if ((st = renorm_(0))) return st;
     if (disc) {
       std::vector<double> after(3 * (size_t)B);
       CK(cudaMemcpyAsync(after.data(), dDisc, sizeof(double) * 3 * B, cudaMemcpyDeviceToHost, stream));
@@ -1484,7 +1502,10 @@ struct Eng : EngBase {
     if ((st = trace_(tr))) return st;
     auto finite = [&](double v) { return std::isfinite(v); };
     if (kind == MPDO_EXPECT_TRACE) {
-      for (int b = 0; b < B; ++b) out[b] = tr[b];
+      std::vector<int> ex(B);
+      CK(cudaMemcpyAsync(ex.data(), dExp2, sizeof(int) * B, cudaMemcpyDeviceToHost, stream));
+      CK(cudaStreamSynchronize(stream));
+      for (int b = 0; b < B; ++b) out[b] = std::ldexp(tr[b], ex[b]);
       return MPDO_OK;
     }
     if (kind == MPDO_EXPECT_ZZ || kind == MPDO_EXPECT_ZZ_MAP || kind == MPDO_EXPECT_MAXCUT) {
@@ -1648,6 +1669,10 @@ struct Eng : EngBase {
     CK(cudaMemcpyAsync(d.data(), dDisc, sizeof(double) * d.size(), cudaMemcpyDeviceToHost, stream));
     CK(cudaStreamSynchronize(stream));
     if (fwrite(d.data(), sizeof(double), d.size(), f) != d.size()) return MPDO_EINVAL;
+    std::vector<int> ex(B);
+    CK(cudaMemcpyAsync(ex.data(), dExp2, sizeof(int) * B, cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    if (fwrite(ex.data(), sizeof(int), ex.size(), f) != ex.size()) return MPDO_EINVAL;
     return MPDO_OK;
   }
   mpdo_status load(FILE* f) override {
@@ -1659,6 +1684,9 @@ struct Eng : EngBase {
     std::vector<double> d(3 * (size_t)B);
     if (fread(d.data(), sizeof(double), d.size(), f) != d.size()) return MPDO_EINVAL;
     CK(cudaMemcpy(dDisc, d.data(), sizeof(double) * d.size(), cudaMemcpyHostToDevice));
+    std::vector<int> ex(B);
+    if (fread(ex.data(), sizeof(int), ex.size(), f) != ex.size()) return MPDO_EINVAL;
+    CK(cudaMemcpy(dExp2, ex.data(), sizeof(int) * ex.size(), cudaMemcpyHostToDevice));
     return MPDO_OK;
   }
 };
@@ -1943,7 +1971,7 @@ mpdo_status expect(mpdo_t h, int kind, const int* args, int nargs, double* out) 
   return h->e->expect(kind, args, nargs, out);
 }
 
-static const char kMagic[8] = {'M', 'P', 'D', 'O', 'C', 'K', 'P', '1'};
+static const char kMagic[8] = {'M', 'P', 'D', 'O', 'C', 'K', 'P', '2'};
 
 mpdo_status mpdo_save(mpdo_t h, const char* path) {
   if (!h || !path) return MPDO_EINVAL;

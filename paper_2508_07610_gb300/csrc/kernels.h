@@ -103,6 +103,11 @@ struct FuseArgs {
 template <typename R>
 cudaError_t fuse_gate(cudaStream_t s, int batch, const FuseArgs<R>& a);
 
+// Keeps each chain's site near unit scale by an exact power of two, accumulated in exp2 (per chain,
+// the stored state times 2^exp2 is the represented one); the site's entries are the first `elems`.
+template <typename R>
+cudaError_t renorm_sites(cudaStream_t s, int batch, int64_t elems, cplx<R>* site, int64_t stride, int* exp2);
+
 // Three-qubit gate on a merged three-site tensor (one thread per output element):
 //   T[x][p1'][p2'][n2][k][n3][p3'][r] = sum_{p1 p2 p3} Khat_k[(p1' p2' p3'), (p1 p2 p3)] T0[x][p1][p2][n2][p3][n3][r]
 // Khat per instance [rk][8][8]; T0 and T the instance strides t0stride, tstride.

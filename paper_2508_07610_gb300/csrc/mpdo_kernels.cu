@@ -197,6 +197,39 @@ __global__ void gate3_kernel(int X, int dn2, int dn3, int dr, int rk, const cplx
   }
 }
 
+// Keeps a site near unit scale: per chain, the binary exponent ex of the largest |Re|, |Im| of the
+// site's `elems` entries; when |ex| > 24 the site is multiplied by 2^-ex (exact) and 2 ex is added to
+// the chain's trace exponent exp2 (the stored state times 2^exp2 is the represented one).
+template <typename R>
+__global__ void renorm_kernel(int64_t elems, cplx<R>* site, int64_t stride, int* exp2) {
+  const int z = blockIdx.x;
+  cplx<R>* S = site + (int64_t)z * stride;
+  __shared__ R red[NT / 32];
+  __shared__ int s_ex;
+  R m = 0;
+  for (int64_t e = threadIdx.x; e < elems; e += NT) m = fmax(m, fmax(fabs(S[e].x), fabs(S[e].y)));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    R mm = 0;
+    for (int w = 0; w < NT / 32; ++w) mm = fmax(mm, red[w]);
+    int ex = 0;
+    if (mm > R(0) && isfinite((double)mm)) frexp(mm, &ex);
+    if (ex > 24 || ex < -24) exp2[z] += 2 * ex;
+    else ex = 0;
+    s_ex = ex;
+  }
+  __syncthreads();
+  if (s_ex != 0) {
+    const R f = ldexp(R(1), -s_ex);
+    for (int64_t e = threadIdx.x; e < elems; e += NT) {
+      S[e].x *= f;
+      S[e].y *= f;
+    }
+  }
+}
+
 // Kraus-leg Gram of a site (or merged pair) with a new Kraus leg, X = (Khat (x) I) A, from the Gram H
 // of A over its bond indices:  G[(k, n), (k', n')] = sum_{p, p''} M_kk'[p, p''] H[(p, n), (p'', n')]
 // with M_kk' = Khat_k^H Khat_k' (d x d, d = 2 for one qubit, 4 for a pair); G column-major (ld rk dn),
@@ -413,6 +446,12 @@ cudaError_t fuse_gate(cudaStream_t s, int batch, const FuseArgs<R>& a) {
   return cudaGetLastError();
 }
 template <typename R>
+cudaError_t renorm_sites(cudaStream_t s, int batch, int64_t elems, cplx<R>* site, int64_t stride, int* exp2) {
+  if (batch <= 0 || elems <= 0) return cudaSuccess;
+  renorm_kernel<R><<<batch, NT, 0, s>>>(elems, site, stride, exp2);
+  return cudaGetLastError();
+}
+template <typename R>
 cudaError_t gate3(cudaStream_t s, int batch, int X, int dn2, int dn3, int dr, int rk, const cplx<R>* Khat,
                   const cplx<R>* T0, int64_t t0stride, cplx<R>* T, int64_t tstride) {
   if (batch <= 0) return cudaSuccess;
@@ -527,6 +566,7 @@ cudaError_t permute(cudaStream_t s, int batch, int nd, const int* dims, const in
 
 #define INST(R)                                                                                                  \
   template cudaError_t fuse_gate<R>(cudaStream_t, int, const FuseArgs<R>&);                                      \
+  template cudaError_t renorm_sites<R>(cudaStream_t, int, int64_t, cplx<R>*, int64_t, int*);                  \
   template cudaError_t gate3<R>(cudaStream_t, int, int, int, int, int, int, const cplx<R>*, const cplx<R>*,      \
                                 int64_t, cplx<R>*, int64_t);                                                     \
   template cudaError_t build_T<R>(cudaStream_t, int, int, const cplx<R>*, const cplx<R>*, int64_t, cplx<R>*,     \

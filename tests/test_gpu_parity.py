@@ -14,11 +14,12 @@ from oracle import dense as OD
 from oracle import mpdo as OM
 from paper_2508_07610_gb300 import mpdo as G
 from paper_2508_07610_gb300 import workloads as W
-from tolerances import allowance, discarded_limit, readout_limit
+from tolerances import MODES, allowance, discarded_limit, readout_limit
 
 pytestmark = pytest.mark.gpu
 
 TRACE_TOL = {"fp64": 1e-10, "mixed": 1e-5, "fp32": 1e-5}
+MODES_READOUT = {k: v[0] for k, v in MODES.items()}
 
 
 def _oracle_from_gpu(st: G.MPDO, chain: int = 0) -> OM.MPDO:
@@ -537,3 +538,27 @@ def test_deep_lossy_qaoa_instance_stays_finite():
         disc = st.discarded()[0]
         assert 0 < disc[0] < 2 * len(c.ops) and 0 < disc[1] < 2 * len(c.ops)
     assert 0 < traces["fp64"] < 1e-6 and 0 < traces["mixed"] < 1e-6
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp32", "fp64"])
+def test_trace_far_below_the_fp32_range(prec):
+    """kappa_max = 1 after strong damping and depolarizing keeps about half of the weight per 1q gate,
+    so 100 layers take Tr rho to about 1e-53: complex64 sites would underflow without the per-chain
+    power-of-two scale, which the TRACE readout multiplies back in.  Every cut is well separated."""
+    rng = np.random.default_rng(1400)
+    n = 4
+    chis = [(1, W.kraus_to_chi(W.compose(W.amplitude_damping(0.5), W.depolarizing_1q(0.6)))),
+            (2, W.kraus_to_chi([np.eye(4)]))]
+    ops = []
+    for layer in range(100):
+        ops += [W.Op(1, q, W.random_unitary(2, rng), 0) for q in range(n)]
+        ops += [W.Op(2, q, W.random_unitary(4, rng), 1) for q in range(layer % 2, n - 1, 2)]
+    circ = W.Circuit(n, ops, chis)
+    st = G.run_circuit(circ, 16, 1, prec)
+    orc = OM.run_circuit(circ, 16, 1)
+    assert orc.trace() < 1e-45 and allowance(orc, prec) == 0
+    # the trace is a product of 400 truncations' kept weights: relative error about 400 times the
+    # per-truncation bound
+    assert abs(st.trace()[0] / orc.trace() - 1) < 400 * TRACE_TOL[prec]
+    zz = st.zz_map()[0]
+    assert np.max(np.abs(zz - orc.zz_map())) < MODES_READOUT[prec]
