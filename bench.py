@@ -34,7 +34,7 @@ METRIC = "2q gate+channel+truncate updates/s at chi=64, kappa=8 (err<=1e-6 vs FP
 # DRAM bytes (read + write) per launch of the single-shape call sites, from an ncu capture of the
 # steady-state workload with 128 chains per handle; valid for the kernels as captured and for 128
 # chains per group
-NCU_TRAFFIC_128 = {"eig_bond": 231.6e6, "gemm_theta": 1353.3e6}
+NCU_TRAFFIC_128 = {"eig_bond": 1.022e9}  # DRAM bytes per launch of 128 chains (ncu, the eigensolver capture in profiles/)
 
 
 def peaks():
