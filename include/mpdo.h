@@ -141,6 +141,18 @@ mpdo_status truncate_bonds(mpdo_t h, int chi, double* discarded);
 /* Readouts (Sec. II.C local densities, Eqs. maxcut / maxcut_obj); out: host, see MPDO_EXPECT_*. */
 mpdo_status expect(mpdo_t h, int kind, const int* args, int nargs, double* out);
 
+/* The whole bitstring distribution <z| rho |z> / Tr rho of every chain (the output distribution the
+ * paper compares with measured data, Sec. IV.A, and between truncation settings, Sec. IV.C): out (host)
+ * receives batch x 2^n values, chain-major, bitstring index with qubit 0 most significant.  All 2^q
+ * prefixes of a chain are carried through site q at once (4 n batched products per chain).  n <= 15
+ * (MPDO_EINVAL otherwise); MPDO_ENOMEM if the prefix environments do not fit; synchronises. */
+mpdo_status mpdo_distribution(mpdo_t h, double* out);
+/* Jensen-Shannon divergence of two distributions over len outcomes (natural log; both normalised
+ * first; 0 log 0 = 0): the distance the paper fits noise models with (Sec. IV.A).  0 for equal
+ * distributions, ln 2 for disjoint supports.  Host computation, no GPU.  MPDO_EINVAL for negative or
+ * non-finite entries or a zero total. */
+mpdo_status mpdo_jsd(const double* p, const double* q, int len, double* out);
+
 /* Uhlmann fidelity F(rho, sigma) = (tr sqrt(sqrt(rho) sigma sqrt(rho)))^2 (Sec. IV.C, Eq. fidelity)
  * between chain chain_a of a and chain chain_b of b, both normalised to unit trace; the paper uses it
  * to compare truncated with untruncated states.  Dense and in FP64 whatever the handles' precision:

@@ -149,6 +149,7 @@ struct EngBase {
   virtual mpdo_status alloc_tc() = 0;
   // dense density matrix of one chain (small n), FP64, see Eng::dense_rho
   virtual int64_t dense_work() const = 0;
+  virtual mpdo_status distribution(double* out) = 0;
   virtual mpdo_status dense_rho(int chain, cudaStream_t s, cplx<double>* X, cplx<double>* Y, cplx<double>* S) = 0;
 
   int* dStatus = nullptr;  // device status word: kStatusNoConv | kStatusTimeout bits set by kernels
@@ -1376,6 +1377,69 @@ struct Eng : EngBase {
     return MPDO_OK;
   }
 
+  // The whole bitstring distribution <z| rho |z> / Tr rho of every chain (Sec. IV.A, IV.C): the
+  // element transfer of element_bits for all 2^q prefixes of a chain at once, prefixes as the batch
+  // of the products, E_{(A, p)}[r, r'] = sum_{l, l', n} E_A[l, l'] T[l, p, n, r] conj(T[l', p, n, r']),
+  // so the distribution costs 4 n batched products per chain instead of one sweep per bitstring.
+  // out: B x 2^n, qubit 0 most significant; n <= 15.
+  mpdo_status distribution(double* out) override {
+    if (n > 15) return MPDO_EINVAL;
+    mpdo_status st = clean();
+    if (st) return st;
+    int64_t eMax = 1, tMax = 1;
+    for (int q = 0; q < n; ++q) {
+      const int64_t P = (int64_t)1 << q;
+      eMax = lmax(eMax, 2 * P * bond[q + 1] * bond[q + 1]);
+      eMax = lmax(eMax, P * bond[q] * bond[q]);
+      tMax = lmax(tMax, P * bond[q] * kraus[q] * bond[q + 1]);
+    }
+    C *E0 = nullptr, *E1 = nullptr, *Tm = nullptr;
+    if (dmalloc(&E0, eMax) != cudaSuccess || dmalloc(&E1, eMax) != cudaSuccess || dmalloc(&Tm, tMax) != cudaSuccess) {
+      if (E0) cudaFree(E0);
+      if (E1) cudaFree(E1);
+      cudaGetLastError();
+      return MPDO_ENOMEM;
+    }
+    const int64_t Z = (int64_t)1 << n;
+    std::vector<C> h((size_t)Z);
+    for (int b = 0; b < B && !st; ++b) {
+      C* Ea = E0;
+      C* Eb = E1;
+      CK(fill<R>(stream, 1, Ea, mk<R>(1, 0)));
+      ++launches;
+      for (int q = 0; q < n && !st; ++q) {
+        const int dl = bond[q], dn = kraus[q], dr = bond[q + 1];
+        const int N = dn * dr, P = 1 << q;
+        const C* A = site_ptr(q) + (int64_t)b * slot_elems;
+        for (int p = 0; p < 2 && !st; ++p) {
+          // Tm[A][l'][(n, r)] = sum_l E_A[l, l'] T[l, p, n, r]
+          View ve = v2((int64_t)dl * dl, 0, 0, 1, 0, 0, dl);
+          View va = v2(0, 0, 0, 2 * N, 0, 0, 1);
+          View vt = row_major(N, (int64_t)dl * N);
+          st = gemm_(dl, N, dl, Ea, ve, A + (int64_t)p * N, va, Tm, vt, P);
+          if (st) break;
+          // E_{(A, p)}[r, r'] = sum_{(l', n)} Tm[A][(l', n), r] conj(T[l', p, n, r'])
+          View vt2 = v2((int64_t)dl * N, 0, 0, 1, 0, 0, dr);
+          View vb = v2(0, dn, (int64_t)2 * N, dr, 0, 0, 1, 1);
+          View vo = row_major(dr, (int64_t)2 * dr * dr);
+          st = gemm_(dr, dr, dl * dn, Tm, vt2, A + (int64_t)p * N, vb, Eb + (int64_t)p * dr * dr, vo, P);
+        }
+        std::swap(Ea, Eb);
+      }
+      if (st) break;
+      CK(cudaMemcpyAsync(h.data(), Ea, sizeof(C) * Z, cudaMemcpyDeviceToHost, stream));
+      CK(cudaStreamSynchronize(stream));
+      double tot = 0;
+      for (int64_t z = 0; z < Z; ++z) tot += (double)h[(size_t)z].x;
+      for (int64_t z = 0; z < Z; ++z) out[(size_t)b * Z + z] = tot > 0 ? (double)h[(size_t)z].x / tot : 0.0;
+      if (!(tot > 0) || !std::isfinite(tot)) st = MPDO_ENOCONV;
+    }
+    cudaFree(E0);
+    cudaFree(E1);
+    cudaFree(Tm);
+    return st;
+  }
+
   // Tr rho^2 by the four-copy transfer (one chain at a time)
   // Tr rho^2 per chain: a left-to-right sweep of the four-copy environment E[a][b][c][d]
   // (ket, bra, ket, bra bond indices; D^4 elements) through four GEMMs per site, each about
@@ -1965,6 +2029,30 @@ mpdo_status truncate_bonds(mpdo_t h, int chi, double* discarded) {
   if (!h) return MPDO_EINVAL;
   if (discarded && h->e->capturing) return MPDO_ESTATE;
   return h->e->truncate_bonds(chi, discarded);
+}
+mpdo_status mpdo_distribution(mpdo_t h, double* out) {
+  if (!h || !out) return MPDO_EINVAL;
+  if (h->e->capturing) return MPDO_ESTATE;
+  return h->e->distribution(out);
+}
+mpdo_status mpdo_jsd(const double* p, const double* q, int len, double* out) {
+  if (!p || !q || !out || len < 1) return MPDO_EINVAL;
+  double sp = 0, sq = 0;
+  for (int i = 0; i < len; ++i) {
+    if (!(p[i] >= 0) || !(q[i] >= 0) || !std::isfinite(p[i]) || !std::isfinite(q[i])) return MPDO_EINVAL;
+    sp += p[i];
+    sq += q[i];
+  }
+  if (!(sp > 0) || !(sq > 0)) return MPDO_EINVAL;
+  // JSD = (KL(p || m) + KL(q || m)) / 2 with m = (p + q) / 2, natural log, 0 log 0 = 0
+  double js = 0;
+  for (int i = 0; i < len; ++i) {
+    const double a = p[i] / sp, b = q[i] / sq, m = 0.5 * (a + b);
+    if (a > 0) js += 0.5 * a * std::log(a / m);
+    if (b > 0) js += 0.5 * b * std::log(b / m);
+  }
+  *out = js;
+  return MPDO_OK;
 }
 mpdo_status expect(mpdo_t h, int kind, const int* args, int nargs, double* out) {
   if (!h || !out) return MPDO_EINVAL;

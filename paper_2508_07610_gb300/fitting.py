@@ -6,7 +6,7 @@ channel on every gate plus amplitude damping on single-qubit gates, theta = (p1,
 the library as process matrices (Eq. chi).  The loss JSD(p(theta), target) and its gradient come from
 the GPU MPDO: the 2P + 1 parameter vectors of a central-difference gradient (steps in log theta) run
 as the chains of one batched handle, each chain with its own channels, and every chain's bitstring
-distribution is read with MPDO_EXPECT_PROB.  The optimiser (Adam in log theta, so strengths stay
+distribution is read in one batched prefix contraction (mpdo_distribution) and compared with mpdo_jsd.  The optimiser (Adam in log theta, so strengths stay
 positive) runs on the host.
 """
 from __future__ import annotations
@@ -36,11 +36,10 @@ class NoiseModelFit:
 
     def __init__(self, n: int, gates: Sequence[Tuple[int, int, np.ndarray]], chi_max: int = 16, kappa_max: int = 8,
                  prec: str = "fp64", step: float = 1e-3):
-        if n > 12:
-            raise ValueError("the loss reads the full 2^n distribution: n <= 12")
+        if n > 15:
+            raise ValueError("the loss reads the full 2^n distribution: n <= 15")
         self.n, self.gates = n, list(gates)
         self.chi_max, self.kappa_max, self.prec, self.step = chi_max, kappa_max, prec, step
-        self.bits = [[(z >> (n - 1 - i)) & 1 for i in range(n)] for z in range(1 << n)]
 
     def distributions(self, thetas: np.ndarray) -> np.ndarray:
         """Bitstring distributions (len(thetas) x 2^n, qubit 0 most significant), one chain per theta."""
@@ -51,7 +50,7 @@ class NoiseModelFit:
         ch2 = st.channels(2, [c[1] for c in chis])
         for kind, q, U in self.gates:
             (st.apply_1q if kind == 1 else st.apply_2q)(q, U, ch1 if kind == 1 else ch2)
-        out = np.stack([st.probability(b) for b in self.bits], axis=1)
+        out = st.distribution()
         ch1.free()
         ch2.free()
         st.free()

@@ -76,6 +76,8 @@ def lib():
         "mpdo_set_trunc_order": [vp, i32],
         "mpdo_tc_selftest": [i32, i32, i32, dp, ip],
         "mpdo_fidelity": [vp, i32, vp, i32, dp],
+        "mpdo_distribution": [vp, dp],
+        "mpdo_jsd": [dp, dp, i32, dp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -284,6 +286,13 @@ class MPDO:
         """<z| rho |z> / Tr rho per chain for the bitstring z (bits[i] is qubit i's outcome)."""
         return self._expect(PROB, tuple(int(v) for v in bits))
 
+    def distribution(self) -> np.ndarray:
+        """The whole bitstring distribution per chain, batch x 2^n (qubit 0 most significant), from one
+        batched prefix contraction (mpdo_distribution; n <= 15)."""
+        out = np.zeros((self.batch, 1 << self.n))
+        _check(lib().mpdo_distribution(self.h, out.ctypes.data_as(C.POINTER(C.c_double))), "mpdo_distribution")
+        return out
+
     def probabilities(self) -> np.ndarray:
         """The full output distribution per chain, batch x 2^n, basis index with qubit 0 most
         significant (small n only: one readout sweep per bitstring)."""
@@ -397,15 +406,13 @@ def run_circuit(circuit, chi_max: int, kappa_max: int, prec="fp64", stream: int 
 
 def jsd(p, q) -> float:
     """Jensen-Shannon divergence (natural log) between two distributions over the same outcomes, the
-    distance the paper uses to compare output distributions: 0 for equal ones, ln 2 for disjoint ones."""
-    p = np.asarray(p, dtype=np.float64)
-    q = np.asarray(q, dtype=np.float64)
-    p = p / p.sum()
-    q = q / q.sum()
-    m = 0.5 * (p + q)
-
-    def kl(a):
-        nz = a > 0
-        return float(np.sum(a[nz] * np.log(a[nz] / m[nz])))
-
-    return 0.5 * kl(p) + 0.5 * kl(q)
+    distance the paper uses to compare output distributions: 0 for equal ones, ln 2 for disjoint ones
+    (mpdo_jsd)."""
+    a = np.ascontiguousarray(p, dtype=np.float64).reshape(-1)
+    b = np.ascontiguousarray(q, dtype=np.float64).reshape(-1)
+    if a.size != b.size:
+        raise ValueError("jsd: distributions of different lengths")
+    out = C.c_double()
+    _check(lib().mpdo_jsd(a.ctypes.data_as(C.POINTER(C.c_double)), b.ctypes.data_as(C.POINTER(C.c_double)),
+                          int(a.size), C.byref(out)), "mpdo_jsd")
+    return out.value

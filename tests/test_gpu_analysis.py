@@ -55,3 +55,28 @@ def test_fidelity_rejects_large_chains():
     a = G.MPDO(8, 4, 2, "fp64")
     with pytest.raises(G.MPDOError):
         a.fidelity(a)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp32"])
+def test_distribution_matches_oracle_and_per_bitstring_readout(prec):
+    """mpdo_distribution (all 2^n prefixes carried through each site at once) against the oracle's
+    dense diagonal, and against the one-sweep-per-bitstring readout."""
+    from tolerances import readout_limit
+    rng = np.random.default_rng(1500)
+    circ = W.random_circuit(5, 18, rng, rank1=3, rank2=5)
+    st = G.run_circuit(circ, 6, 3, prec)
+    orc = OM.run_circuit(circ, 6, 3)
+    d = st.distribution()
+    ref = np.real(np.diag(orc.dense()))
+    ref = ref / ref.sum()
+    assert d.shape == (1, 32) and abs(d.sum() - 1) < 1e-12
+    assert np.max(np.abs(d[0] - ref)) < readout_limit(orc, prec)
+    per = np.array([st.probability([(z >> (4 - i)) & 1 for i in range(5)])[0] for z in range(32)])
+    assert np.max(np.abs(d[0] - per)) < 2 * readout_limit(orc, prec)
+    assert G.jsd(d[0], ref) < 1e-6
+
+
+def test_distribution_rejects_long_chains():
+    st = G.MPDO(16, 2, 2, "fp64")
+    with pytest.raises(G.MPDOError):
+        st.distribution()
