@@ -27,6 +27,8 @@
 #ifndef MPDO_H
 #define MPDO_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -46,7 +48,9 @@ typedef enum {
                         eigenpairs, or a readout came out non-finite */
   MPDO_ETIMEOUT = 6, /* a bounded wait inside a kernel (tensor-core pipelines) ran out */
   MPDO_ECUDA = 7,    /* CUDA runtime error */
-  MPDO_ESTATE = 8    /* call not valid in the handle's current state (e.g. during capture) */
+  MPDO_ESTATE = 8,   /* call not valid in the handle's current state (e.g. during capture) */
+  MPDO_EDRIFT = 9    /* the trace guard (mpdo_set_trace_guard) saw Tr rho grow, or turn negative or
+                        non-finite, over one call */
 } mpdo_status;
 
 typedef enum {
@@ -206,6 +210,19 @@ mpdo_status mpdo_set_trunc_order(mpdo_t h, int order);
  * read when each call is made). */
 mpdo_status mpdo_set_neighbour_truncation(mpdo_t h, int enable);
 
+/* Trace guard, a debugging aid: with tol > 0, every apply_* and truncate_* call made outside graph
+ * capture reads Tr rho of every chain afterwards (the TRACE readout, so the call synchronises) and
+ * compares it with the value after the previous guarded call.  The channels are trace preserving and
+ * a truncation only removes weight, so Tr rho never grows in exact arithmetic: the call returns
+ * MPDO_EDRIFT (after its work is done) when a chain's trace exceeds the previous one by more than
+ * tol relative, or is negative or non-finite.  Rounding moves the trace by about 1e-6 relative per
+ * call in the complex64 modes and 1e-12 in FP64, and an accepted channel may be trace preserving to
+ * 1e-8 only: 1e-4 and 1e-7 are suitable tolerances.  Enabling takes the current traces as the
+ * baseline, mpdo_reset sets it to 1; an edit of the state between guarded calls (mpdo_set_site) is
+ * measured at the next guarded call, so call this again after such an edit to take a new baseline.
+ * tol <= 0 switches the guard off (the default).  MPDO_ESTATE during capture. */
+mpdo_status mpdo_set_trace_guard(mpdo_t h, double tol);
+
 /* Device memory the PURITY readout may hold for its intermediates, in bytes (0, the default: 35% of
  * the device memory free at its first call).  The purity contraction carries a chi^4 environment
  * and intermediates of up to 2 kappa chi^5 elements per site; they are processed in chunks of one
@@ -272,6 +289,29 @@ mpdo_status mpdo_tc_selftest(int M, int N, int K, double* max_rel_err, int* err_
  * wait gives up, the kernel records the timeout in a status word and returns: MPDO_ETIMEOUT, with
  * the word in *status_out.  Demonstrates that no wait in the library can hang the GPU. */
 mpdo_status mpdo_wait_selftest(int limit_us, int* status_out);
+
+/* ---- Address-checked debug build.  libmpdo_bounds.so is this library compiled from the same
+ * sources with -DMPDO_BOUNDS (paper_2508_07610_gb300.build.build(bounds=True)).  In it every global
+ * memory access of the MPDO kernels first checks that its bytes lie inside a live device range: an
+ * allocation the library made, or a range the caller registered.  A failed check is counted, the
+ * first one is recorded, and the access goes to a scratch buffer instead: no trap, no fault, and the
+ * results of that call are meaningless.  The release library compiles none of this.
+ *
+ * mpdo_bounds_enabled: 1 in the checked build, 0 in the release library.
+ * mpdo_bounds_register(p, bytes): a caller-owned device buffer the kernels may read (the U_dev and
+ *   chan_idx_dev arrays of the batched forms, the buffers of channel_kraus_noalloc); ranges may
+ *   overlap.  mpdo_bounds_unregister(p) removes the range registered at p (MPDO_EINVAL if none).
+ *   Both are no-ops returning MPDO_OK in the release library.
+ * mpdo_bounds_read: synchronises the device, returns the number of failed checks since the last call
+ *   in *failures and clears it; the first failure's source file name (at most file_cap - 1
+ *   characters), line, address and access size go to the other outputs (each nullable).  MPDO_ENOMEM
+ *   when more than 16384 disjoint ranges were live at once (checking then switched off), MPDO_ESTATE
+ *   in the release library. */
+int mpdo_bounds_enabled(void);
+mpdo_status mpdo_bounds_register(const void* p, size_t bytes);
+mpdo_status mpdo_bounds_unregister(const void* p);
+mpdo_status mpdo_bounds_read(unsigned long long* failures, char* file, int file_cap, int* line,
+                             unsigned long long* addr, unsigned long long* bytes);
 
 /* ---- Batched runtime: many independent noisy circuits ("instances") on one GPU.  The paper runs one
  * circuit at a time; this is the throughput form of the same per-gate update (Sec. II.C-II.D).

@@ -24,6 +24,7 @@
 #include <string>
 #include <vector>
 
+#include "bounds.cuh"
 #include "mpdo.h"
 
 namespace {

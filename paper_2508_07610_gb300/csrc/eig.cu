@@ -117,17 +117,18 @@ __global__ void __launch_bounds__(NT, 2) heevk_kernel(EigArgs<R> g) {
   const int n = g.n, k = g.k;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   if (tid == 0) s_bad = 0;
-  cplx<R>* A = g.A + (int64_t)z * g.astride;
-  R* S = g.scratch + (int64_t)z * g.sstride;
+  GPTR(cplx<R>, A, g.A + (int64_t)z * g.astride);
+  R* const S = g.scratch + (int64_t)z * g.sstride;
+  const int64_t nk = (int64_t)n * k;
   // scratch layout (R units, vector t element i at [i * k + t] so threads walk it coalesced)
-  R* Ldl = S;
-  R* Ldd = Ldl + (int64_t)n * k;
-  R* Ldu = Ldd + (int64_t)n * k;
-  R* Ldu2 = Ldu + (int64_t)n * k;
-  R* Lpiv = Ldu2 + (int64_t)n * k;
-  R* Zr = Lpiv + (int64_t)n * k;
-  cplx<R>* U = reinterpret_cast<cplx<R>*>(Zr + (int64_t)n * k);   // complex, vector t column at [t * n]
-  cplx<R>* PH = U + (int64_t)n * k;                                  // phases, n
+  GPTR(R, Ldl, S);
+  GPTR(R, Ldd, S + nk);
+  GPTR(R, Ldu, S + 2 * nk);
+  GPTR(R, Ldu2, S + 3 * nk);
+  GPTR(R, Lpiv, S + 4 * nk);
+  GPTR(R, Zr, S + 5 * nk);
+  GPTR(cplx<R>, U, reinterpret_cast<cplx<R>*>(S + 6 * nk));        // complex, vector t column at [t * n]
+  GPTR(cplx<R>, PH, reinterpret_cast<cplx<R>*>(S + 6 * nk) + nk);  // phases, n
 
   // ---- (0) scale.  The safeguards below (pivot minimum, the zero test of Householder norms, the FP32
   // bracket) are absolute, so the matrix is first multiplied by the power of two that brings its
@@ -168,7 +169,7 @@ __global__ void __launch_bounds__(NT, 2) heevk_kernel(EigArgs<R> g) {
     const int pb = (n - 2 - j0 < NB) ? n - 2 - j0 : NB;
     for (int jj = 0; jj < pb; ++jj) {
       const int j = j0 + jj;
-      cplx<R>* col = A + (int64_t)j * n;
+      auto col = A + (int64_t)j * n;
       // column j (rows j..n-1) brought up to date and written back
       for (int i = j + tid; i < n; i += NT) {
         cplx<R> c = col[i];
@@ -232,7 +233,7 @@ __global__ void __launch_bounds__(NT, 2) heevk_kernel(EigArgs<R> g) {
           }
           __syncthreads();
           for (int i = j + 1 + wid; i + 1 < n; i += NT / 32) {
-            const cplx<R>* coli = A + (int64_t)i * n;
+            const auto coli = A + (int64_t)i * n;
             cplx<R> dot = mk<R>(0, 0);
             for (int c = i + 1 + lane; c < n; c += 32) cfma_cj(dot, coli[c], s_v[c]);
             dot = panel::warp_csum(dot);
@@ -680,7 +681,7 @@ __global__ void __launch_bounds__(NT, 2) heevk_kernel(EigArgs<R> g) {
   }
 
   // ---- outputs
-  cplx<R>* V = g.V + view_batch(g.vv, z);
+  GPTR(cplx<R>, V, g.V + view_batch(g.vv, z));
   for (int64_t e = tid; e < (int64_t)n * k; e += NT) {
     int i = (int)(e % n), t = (int)(e / n);
     cplx<R> v = U[(int64_t)t * n + i];
@@ -688,7 +689,7 @@ __global__ void __launch_bounds__(NT, 2) heevk_kernel(EigArgs<R> g) {
     V[view_row(g.vv, i) + view_col(g.vv, t)] = v;
   }
   if (g.w) {
-    R* w = g.w + (int64_t)z * g.wstride;
+    GPTR(R, w, g.w + (int64_t)z * g.wstride);
     for (int t = tid; t < k; t += NT) w[t] = ldexp(s_w[t], s_exp);
   }
   // non-finite eigenvalues, trace or eigenvector entries (from non-finite input: the inverse
@@ -701,16 +702,16 @@ __global__ void __launch_bounds__(NT, 2) heevk_kernel(EigArgs<R> g) {
   if (tid == 0) {
     double kept = 0;
     for (int t = 0; t < k; ++t) kept += (double)s_w[t];
-    if (g.status && (s_bad || !isfinite(kept) || !isfinite((double)trace))) atomicOr(g.status, kStatusNoConv);
+    if (g.status && (s_bad || !isfinite(kept) || !isfinite((double)trace))) atomicOr(GP(g.status), kStatusNoConv);
     double tr = (double)trace;
     if (g.disc && tr > 0) {
       double w = (tr - kept) / tr;
       if (w < 0) w = 0;
-      g.disc[(int64_t)z * g.disc_stride] += w;
+      GX(g.disc, (int64_t)z * g.disc_stride) += w;
     }
     if (g.gap && k < n && s_w[0] > R(0)) {
       double gp = ((double)s_w[k - 1] - (double)s_w[k]) / (double)s_w[0];
-      double* gz = g.gap + (int64_t)z * g.disc_stride;
+      double* gz = GP(g.gap + (int64_t)z * g.disc_stride);
       if (gp < *gz) *gz = gp;
     }
   }

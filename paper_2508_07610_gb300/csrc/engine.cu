@@ -1768,8 +1768,26 @@ EngBase* make_engine(int prec) {
 
 struct mpdo_ctx {
   EngBase* e = nullptr;
+  double guard_tol = 0;             // trace guard: off when <= 0
+  std::vector<double> guard_last;   // Tr rho of every chain after the previous guarded call
   ~mpdo_ctx() { delete e; }
 };
+
+// The trace guard after a gate or truncation that returned `st`: reads Tr rho of every chain and
+// compares it with the reading after the previous guarded call.  The channels are trace preserving and
+// truncations only drop weight, so a growth beyond the tolerance (or a negative or non-finite trace)
+// means the call went wrong.  A trace that underflowed to 0 passes.
+static mpdo_status guard_after(mpdo_ctx* h, mpdo_status st) {
+  if (st != MPDO_OK || !(h->guard_tol > 0) || h->e->capturing) return st;
+  std::vector<double> tr(h->e->B);
+  st = h->e->expect(MPDO_EXPECT_TRACE, nullptr, 0, tr.data());
+  if (st) return st;
+  bool bad = false;
+  for (int b = 0; b < h->e->B; ++b)
+    if (!(tr[b] >= 0) || !std::isfinite(tr[b]) || tr[b] > h->guard_last[b] * (1.0 + h->guard_tol)) bad = true;
+  h->guard_last = tr;
+  return bad ? MPDO_EDRIFT : MPDO_OK;
+}
 
 // ====================================================================== C ABI
 extern "C" {
@@ -1785,6 +1803,7 @@ const char* mpdo_status_string(int s) {
     case MPDO_ETIMEOUT: return "timeout";
     case MPDO_ECUDA: return "CUDA error";
     case MPDO_ESTATE: return "invalid state for this call";
+    case MPDO_EDRIFT: return "trace guard: Tr rho grew or became non-finite";
   }
   return "unknown status";
 }
@@ -1832,7 +1851,9 @@ mpdo_status mpdo_free(mpdo_t h) {
 
 mpdo_status mpdo_reset(mpdo_t h) {
   if (!h) return MPDO_EINVAL;
-  return h->e->reset();
+  mpdo_status st = h->e->reset();
+  if (st == MPDO_OK && h->guard_tol > 0) h->guard_last.assign(h->e->B, 1.0);
+  return st;
 }
 
 mpdo_status mpdo_sync(mpdo_t h) {
@@ -1998,37 +2019,37 @@ mpdo_status channel_free(mpdo_chan_t ch) {
 
 mpdo_status apply_1q(mpdo_t h, int q, const double* U, mpdo_chan_t ch) {
   if (!h || !U) return MPDO_EINVAL;
-  return h->e->apply(1, q, U, nullptr, ch, nullptr);
+  return guard_after(h, h->e->apply(1, q, U, nullptr, ch, nullptr));
 }
 mpdo_status apply_2q(mpdo_t h, int q, const double* U, mpdo_chan_t ch) {
   if (!h || !U) return MPDO_EINVAL;
-  return h->e->apply(2, q, U, nullptr, ch, nullptr);
+  return guard_after(h, h->e->apply(2, q, U, nullptr, ch, nullptr));
 }
 mpdo_status apply_3q(mpdo_t h, int q, const double* U, mpdo_chan_t ch) {
   if (!h || !U) return MPDO_EINVAL;
-  return h->e->apply(3, q, U, nullptr, ch, nullptr);
+  return guard_after(h, h->e->apply(3, q, U, nullptr, ch, nullptr));
 }
 mpdo_status apply_3q_batch(mpdo_t h, int q, const double* U_dev, mpdo_chan_t ch, const int* chan_idx_dev) {
   if (!h || !U_dev) return MPDO_EINVAL;
-  return h->e->apply(3, q, nullptr, U_dev, ch, chan_idx_dev);
+  return guard_after(h, h->e->apply(3, q, nullptr, U_dev, ch, chan_idx_dev));
 }
 mpdo_status apply_1q_batch(mpdo_t h, int q, const double* U_dev, mpdo_chan_t ch, const int* chan_idx_dev) {
   if (!h || !U_dev) return MPDO_EINVAL;
-  return h->e->apply(1, q, nullptr, U_dev, ch, chan_idx_dev);
+  return guard_after(h, h->e->apply(1, q, nullptr, U_dev, ch, chan_idx_dev));
 }
 mpdo_status apply_2q_batch(mpdo_t h, int q, const double* U_dev, mpdo_chan_t ch, const int* chan_idx_dev) {
   if (!h || !U_dev) return MPDO_EINVAL;
-  return h->e->apply(2, q, nullptr, U_dev, ch, chan_idx_dev);
+  return guard_after(h, h->e->apply(2, q, nullptr, U_dev, ch, chan_idx_dev));
 }
 mpdo_status truncate_kraus(mpdo_t h, int q, int kappa, double* discarded) {
   if (!h) return MPDO_EINVAL;
   if (discarded && h->e->capturing) return MPDO_ESTATE;
-  return h->e->truncate(q, kappa, discarded);
+  return guard_after(h, h->e->truncate(q, kappa, discarded));
 }
 mpdo_status truncate_bonds(mpdo_t h, int chi, double* discarded) {
   if (!h) return MPDO_EINVAL;
   if (discarded && h->e->capturing) return MPDO_ESTATE;
-  return h->e->truncate_bonds(chi, discarded);
+  return guard_after(h, h->e->truncate_bonds(chi, discarded));
 }
 mpdo_status mpdo_distribution(mpdo_t h, double* out) {
   if (!h || !out) return MPDO_EINVAL;
@@ -2327,6 +2348,22 @@ mpdo_status mpdo_set_trunc_order(mpdo_t h, int order) {
 mpdo_status mpdo_set_neighbour_truncation(mpdo_t h, int enable) {
   if (!h) return MPDO_EINVAL;
   h->e->neighbour_trunc = enable != 0;
+  return MPDO_OK;
+}
+
+mpdo_status mpdo_set_trace_guard(mpdo_t h, double tol) {
+  if (!h || std::isnan(tol)) return MPDO_EINVAL;
+  if (h->e->capturing) return MPDO_ESTATE;
+  if (!(tol > 0)) {
+    h->guard_tol = 0;
+    h->guard_last.clear();
+    return MPDO_OK;
+  }
+  std::vector<double> tr(h->e->B);
+  mpdo_status st = h->e->expect(MPDO_EXPECT_TRACE, nullptr, 0, tr.data());
+  if (st) return st;
+  h->guard_tol = tol;
+  h->guard_last = tr;
   return MPDO_OK;
 }
 

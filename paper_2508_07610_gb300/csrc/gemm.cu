@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(NT, 2) gemm_kernel(GemmArgs<R> g, int a_m_fast
       const int k = k0 + ak;
       const int64_t ro = rowA[ai];
       const bool ok = ro >= 0 && k < ke;
-      cp_elem(as + ak * SA + ai, ok ? A + ro + view_col(g.va, k) : A, ok);
+      cp_elem(as + ak * SA + ai, ok ? GP(A + ro + view_col(g.va, k)) : A, ok);
     }
 #pragma unroll
     for (int t = 0; t < LB; ++t) {
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(NT, 2) gemm_kernel(GemmArgs<R> g, int a_m_fast
       const int k = k0 + bk;
       const int64_t co = colB[bj];
       const bool ok = co >= 0 && k < ke;
-      cp_elem(bs + bk * SB + bj, ok ? B + co + view_row(g.vb, k) : B, ok);
+      cp_elem(bs + bk * SB + bj, ok ? GP(B + co + view_row(g.vb, k)) : B, ok);
     }
   };
 
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(NT, 2) gemm_kernel(GemmArgs<R> g, int a_m_fast
         if (j >= g.N) continue;
         cplx<R> sum = acc[r][c];
         if constexpr (COMP) sum = sum + comp[r][c];
-        P[(int64_t)i * g.N + j] = sum;
+        GX(P, (int64_t)i * g.N + j) = sum;
       }
     }
     return;
@@ -208,12 +208,12 @@ __global__ void __launch_bounds__(NT, 2) gemm_kernel(GemmArgs<R> g, int a_m_fast
       if constexpr (COMP) sum = sum + comp[r][c];
       cplx<R> v = g.alpha * sum;
       if (use_beta) {
-        cplx<R> old = C[o];
+        cplx<R> old = GX(C, o);
         if (g.vc.conj) old.y = -old.y;
         v = v + g.beta * old;
       }
       if (g.vc.conj) v.y = -v.y;
-      C[o] = v;
+      GX(C, o) = v;
     }
   }
 }
@@ -232,19 +232,19 @@ __global__ void splitk_reduce_kernel(GemmArgs<R> g, int sk) {
     if (g.herm && j > i) continue;
     double sx = 0, sy = 0;
     for (int t = 0; t < sk; ++t) {
-      const cplx<R> p = P[t * MN + e];
+      const cplx<R> p = GX(P, t * MN + e);
       sx += (double)p.x;
       sy += (double)p.y;
     }
     cplx<R> v = g.alpha * mk<R>((R)sx, (R)sy);
     const int64_t o = view_row(g.vc, i) + view_col(g.vc, j);
     if (use_beta) {
-      cplx<R> old = C[o];
+      cplx<R> old = GX(C, o);
       if (g.vc.conj) old.y = -old.y;
       v = v + g.beta * old;
     }
     if (g.vc.conj) v.y = -v.y;
-    C[o] = v;
+    GX(C, o) = v;
   }
 }
 

@@ -44,10 +44,10 @@ __global__ void chi_to_choi_kernel(int count, int nq, const cplx<double>* chi, c
       for (int n = 0; n < d2; ++n) {
         cplx<double> sn = pauli_elem(nq, n, bi, bj);
         if (sn.x == 0.0 && sn.y == 0.0) continue;
-        acc = acc + X[m * d2 + n] * sm * conjg(sn);
+        acc = acc + GX(X, m * d2 + n) * sm * conjg(sn);
       }
     }
-    L[e] = acc;
+    GX(L, e) = acc;
   }
 }
 
@@ -56,15 +56,15 @@ __global__ void choi_to_kraus_kernel(int count, int nq, int rmax, const int* r_d
   const int d = 1 << nq, d2 = d * d;
   const int c = blockIdx.x;
   if (c >= count) return;
-  const int r = r_dev[c];
+  const int r = GX(r_dev, c);
   for (int e = threadIdx.x; e < rmax * d2; e += blockDim.x) {
     int i = e / d2, a = e % d2;  // K_i[row][col] with a = row * d + col (row-major vec)
     cplx<double> v = mk<double>(0, 0);
     if (i < r) {
-      double s = sqrt(fmax(eta[(int64_t)c * d2 + i], 0.0));
-      v = s * vecs[(int64_t)c * d2 * d2 + a + (int64_t)i * d2];
+      double s = sqrt(fmax(GX(eta, (int64_t)c * d2 + i), 0.0));
+      v = s * GX(vecs, (int64_t)c * d2 * d2 + a + (int64_t)i * d2);
     }
-    kraus[(int64_t)c * rmax * d2 + e] = v;
+    GX(kraus, (int64_t)c * rmax * d2 + e) = v;
   }
 }
 
@@ -78,10 +78,10 @@ __global__ void kraus_tp_kernel(int count, int nq, int rmax, const cplx<double>*
     for (int b = 0; b < d; ++b) {
       cplx<double> s = mk<double>(a == b ? -1.0 : 0.0, 0.0);
       for (int i = 0; i < rmax; ++i)
-        for (int t = 0; t < d; ++t) cfma_cj(s, K[i * d2 + t * d + a], K[i * d2 + t * d + b]);
+        for (int t = 0; t < d; ++t) cfma_cj(s, GX(K, i * d2 + t * d + a), GX(K, i * d2 + t * d + b));
       e = fmax(e, sqrt(norm2(s)));
     }
-  err[c] = e;
+  GX(err, c) = e;
 }
 
 template <typename R>
@@ -90,14 +90,14 @@ __global__ void fuse_kernel(FuseArgs<R> a) {
   const int d = 1 << a.nq, dd = d * d;
   __shared__ cplx<double> Kh[16 * 16];
   const cplx<double>* U = a.Udev ? a.Udev + (int64_t)z * dd : a.U;
-  const int ch = a.chan_idx ? a.chan_idx[z] : 0;
+  const int ch = a.chan_idx ? GX(a.chan_idx, z) : 0;
   const cplx<double>* N = a.kraus + (int64_t)ch * a.chan_stride;
   for (int e = threadIdx.x; e < a.rk * dd; e += blockDim.x) {
     int k = e / dd, i = (e % dd) / d, j = e % d;
     cplx<double> acc = mk<double>(0, 0);
-    for (int t = 0; t < d; ++t) cfma(acc, N[k * dd + i * d + t], U[t * d + j]);
+    for (int t = 0; t < d; ++t) cfma(acc, GX(N, k * dd + i * d + t), a.Udev ? GX(U, t * d + j) : U[t * d + j]);
     if (a.nq == 2) Kh[e] = acc;  // the reduced superoperator below needs the 2q operators only
-    a.Khat[(int64_t)z * a.rk * dd + e] = mk<R>((R)acc.x, (R)acc.y);
+    GX(a.Khat, (int64_t)z * a.rk * dd + e) = mk<R>((R)acc.x, (R)acc.y);
   }
   __syncthreads();
   if (a.nq == 2 && a.Rt) {
@@ -109,7 +109,7 @@ __global__ void fuse_kernel(FuseArgs<R> a) {
       for (int k = 0; k < a.rk; ++k)
         for (int p2 = 0; p2 < 2; ++p2)
           cfma_cj(acc, Kh[k * 16 + (rb * 2 + p2) * 4 + qq], Kh[k * 16 + (ra * 2 + p2) * 4 + pp]);
-      a.Rt[(int64_t)z * 64 + e] = mk<R>((R)acc.x, (R)acc.y);
+      GX(a.Rt, (int64_t)z * 64 + e) = mk<R>((R)acc.x, (R)acc.y);
     }
   }
 }
@@ -132,9 +132,9 @@ __global__ void build_T_kernel(int dm, const cplx<R>* Rt, const cplx<R>* E, int6
     cplx<R> acc = mk<R>(0, 0);
     for (int p2 = 0; p2 < 2; ++p2)
       for (int q2 = 0; q2 < 2; ++q2)
-        cfma(acc, Rz[(a * 2 + b) * 16 + (p1 * 2 + p2) * 4 + (q1 * 2 + q2)],
-             Ez[(int64_t)(bb * 2 + p2) * C2 + (bbp * 2 + q2)]);
-    Tz[e] = acc;
+        cfma(acc, GX(Rz, (a * 2 + b) * 16 + (p1 * 2 + p2) * 4 + (q1 * 2 + q2)),
+             GX(Ez, (int64_t)(bb * 2 + p2) * C2 + (bbp * 2 + q2)));
+    GX(Tz, e) = acc;
   }
 }
 
@@ -157,8 +157,8 @@ __global__ void build_Y_kernel(int kchi, int dm, int rk, const cplx<R>* Khat, co
     cplx<R> acc = mk<R>(0, 0);
     for (int p1p = 0; p1p < 2; ++p1p)
       for (int p1 = 0; p1 < 2; ++p1)
-        cfma(acc, K[k * 16 + (p1p * 2 + p2p) * 4 + (p1 * 2 + p2)], Hz[(int64_t)(bp * 2 + p1p) * C2 + (p1 * dm + bb)]);
-    Yz[e] = acc;
+        cfma(acc, GX(K, k * 16 + (p1p * 2 + p2p) * 4 + (p1 * 2 + p2)), GX(Hz, (int64_t)(bp * 2 + p1p) * C2 + (p1 * dm + bb)));
+    GX(Yz, e) = acc;
   }
 }
 
@@ -191,9 +191,9 @@ __global__ void gate3_kernel(int X, int dn2, int dn3, int dr, int rk, const cplx
     for (int b = 0; b < 8; ++b) {
       const int b1 = b >> 2, b2 = (b >> 1) & 1, b3 = b & 1;
       const int64_t src = (((((x * 2 + b1) * 2 + b2) * dn2 + n2) * 2 + b3) * dn3 + n3) * dr + r;
-      cfma(acc, Kk[b], Tz0[src]);
+      cfma(acc, GX(Kk, b), GX(Tz0, src));
     }
-    Tz[e] = acc;
+    GX(Tz, e) = acc;
   }
 }
 
@@ -207,7 +207,10 @@ __global__ void renorm_kernel(int64_t elems, cplx<R>* site, int64_t stride, int*
   __shared__ R red[NT / 32];
   __shared__ int s_ex;
   R m = 0;
-  for (int64_t e = threadIdx.x; e < elems; e += NT) m = fmax(m, fmax(fabs(S[e].x), fabs(S[e].y)));
+  for (int64_t e = threadIdx.x; e < elems; e += NT) {
+    const cplx<R> v = GX(S, e);
+    m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+  }
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
   __syncthreads();
@@ -216,7 +219,7 @@ __global__ void renorm_kernel(int64_t elems, cplx<R>* site, int64_t stride, int*
     for (int w = 0; w < NT / 32; ++w) mm = fmax(mm, red[w]);
     int ex = 0;
     if (mm > R(0) && isfinite((double)mm)) frexp(mm, &ex);
-    if (ex > 24 || ex < -24) exp2[z] += 2 * ex;
+    if (ex > 24 || ex < -24) GX(exp2, z) += 2 * ex;
     else ex = 0;
     s_ex = ex;
   }
@@ -224,8 +227,9 @@ __global__ void renorm_kernel(int64_t elems, cplx<R>* site, int64_t stride, int*
   if (s_ex != 0) {
     const R f = ldexp(R(1), -s_ex);
     for (int64_t e = threadIdx.x; e < elems; e += NT) {
-      S[e].x *= f;
-      S[e].y *= f;
+      cplx<R>& v = GX(S, e);
+      v.x *= f;
+      v.y *= f;
     }
   }
 }
@@ -250,10 +254,10 @@ __global__ void kraus_gram_kernel(int d, int rk, int dn, const cplx<R>* Khat, co
     for (int p = 0; p < d; ++p)
       for (int pp = 0; pp < d; ++pp) {
         cplx<R> m = mk<R>(0, 0);
-        for (int t = 0; t < d; ++t) cfma_cj(m, K[k * dd + t * d + p], K[k2 * dd + t * d + pp]);
-        cfma(acc, m, Hz[(int64_t)(p * dn + n) * NH + pp * dn + n2]);
+        for (int t = 0; t < d; ++t) cfma_cj(m, GX(K, k * dd + t * d + p), GX(K, k2 * dd + t * d + pp));
+        cfma(acc, m, GX(Hz, (int64_t)(p * dn + n) * NH + pp * dn + n2));
       }
-    Gz[e] = acc;
+    GX(Gz, e) = acc;
   }
 }
 
@@ -271,17 +275,18 @@ __global__ void kraus_fold_kernel(int d, int rk, int dn, int kap, const cplx<R>*
     const int i = e / cols, j = e % cols;
     const int pq = i / kap, nu = i % kap, p = j / dn, n = j % dn;
     cplx<R> acc = mk<R>(0, 0);
-    for (int k = 0; k < rk; ++k) cfma(acc, K[k * dd + pq * d + p], Vz[(int64_t)(k * dn + n) + (int64_t)nu * vld]);
-    Wz[e] = acc;
+    for (int k = 0; k < rk; ++k) cfma(acc, GX(K, k * dd + pq * d + p), GX(Vz, (int64_t)(k * dn + n) + (int64_t)nu * vld));
+    GX(Wz, e) = acc;
   }
 }
 
 // V[:, j] *= s[j] for a column-major n x n matrix (FP64)
 __global__ void scale_cols_kernel(int n, cplx<double>* V, const double* s) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n; e += (int64_t)gridDim.x * blockDim.x) {
-    const double f = s[e / n];
-    V[e].x *= f;
-    V[e].y *= f;
+    const double f = GX(s, e / n);
+    cplx<double>& v = GX(V, e);
+    v.x *= f;
+    v.y *= f;
   }
 }
 
@@ -293,10 +298,10 @@ __global__ void copy_view_kernel(int M, int N, const cplx<R>* in, View vin, cplx
   const int64_t total = (int64_t)M * N;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     int i = (int)(e / N), j = (int)(e % N);
-    cplx<R> v = I[view_row(vin, i) + view_col(vin, j)];
+    cplx<R> v = GX(I, view_row(vin, i) + view_col(vin, j));
     if (vin.conj) v.y = -v.y;
     if (vout.conj) v.y = -v.y;
-    O[view_row(vout, i) + view_col(vout, j)] = v;
+    GX(O, view_row(vout, i) + view_col(vout, j)) = v;
   }
 }
 
@@ -304,21 +309,23 @@ template <typename R>
 __global__ void scale_odd_kernel(int64_t len, int64_t div, R sgn, cplx<R>* x, int64_t stride) {
   cplx<R>* X = x + (int64_t)blockIdx.y * stride;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x)
-    if ((e / div) % 2 == 1) X[e] = sgn * X[e];
+    if ((e / div) % 2 == 1) GX(X, e) = sgn * GX(X, e);
 }
 
 template <typename A, typename B>
 __global__ void convert_kernel(int64_t count, const cplx<A>* in, cplx<B>* out) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
-    out[e] = mk<B>((B)in[e].x, (B)in[e].y);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+    const cplx<A> v = GX(in, e);
+    GX(out, e) = mk<B>((B)v.x, (B)v.y);
+  }
 }
 
 template <typename R>
 __global__ void init_zero_kernel(int count, cplx<R>* base, int64_t stride) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= count) return;
-  base[(int64_t)c * stride] = mk<R>(1, 0);
-  base[(int64_t)c * stride + 1] = mk<R>(0, 0);
+  GX(base, (int64_t)c * stride) = mk<R>(1, 0);
+  GX(base, (int64_t)c * stride + 1) = mk<R>(0, 0);
 }
 
 template <typename R>
@@ -330,7 +337,7 @@ __global__ void dot_kernel(int64_t len, const cplx<R>* a, int64_t astride, const
   const cplx<R>* B = b + (int64_t)z * bstride;
   double sx = 0, sy = 0;
   for (int64_t e = threadIdx.x; e < len; e += NT) {
-    cplx<R> u = A[e], v = B[e];
+    cplx<R> u = GX(A, e), v = GX(B, e);
     sx += (double)u.x * v.x + (double)u.y * v.y;
     sy += (double)u.x * v.y - (double)u.y * v.x;
   }
@@ -349,14 +356,14 @@ __global__ void dot_kernel(int64_t len, const cplx<R>* a, int64_t astride, const
       tx += rx[w];
       ty += ry[w];
     }
-    out[z] = mk<double>(tx, ty);
+    GX(out, z) = mk<double>(tx, ty);
   }
 }
 
 template <typename R>
 __global__ void fill_kernel(int64_t count, cplx<R>* x, cplx<R> v) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
-    x[e] = v;
+    GX(x, e) = v;
 }
 
 template <typename R>
@@ -365,16 +372,16 @@ __global__ void herm_fill_kernel(int n, cplx<R>* A, int64_t stride) {
   const int64_t total = (int64_t)n * n;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     int i = (int)(e % n), j = (int)(e / n);
-    if (i < j) M[e] = conjg(M[(int64_t)i * n + j]);
+    if (i < j) GX(M, e) = conjg(GX(M, (int64_t)i * n + j));
   }
 }
 
 __global__ void init_disc_kernel(int batch, double* d) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= batch) return;
-  d[3 * b] = 0.0;
-  d[3 * b + 1] = 0.0;
-  d[3 * b + 2] = 1e300;
+  GX(d, 3 * b) = 0.0;
+  GX(d, 3 * b + 1) = 0.0;
+  GX(d, 3 * b + 2) = 1e300;
 }
 
 struct PermDesc {
@@ -395,7 +402,7 @@ __global__ void permute_kernel(PermDesc p, int64_t total, const cplx<R>* in, int
       t /= p.dims[q];
       o += idx * p.ostr[q];
     }
-    O[o] = I[e];
+    GX(O, o) = GX(I, e);
   }
 }
 

@@ -36,8 +36,8 @@ __global__ void prune_and_build_kraus(int count, int nq, double tol, const doubl
   const int c = blockIdx.x;
   if (c >= count) return;
   const int d = 1 << nq, d2 = d * d;
-  const double* w = eta + (int64_t)c * d2;
-  cplx<double>* K = kraus + (int64_t)c * d2 * d2;
+  GPTR(const double, w, eta + (int64_t)c * d2);
+  GPTR(cplx<double>, K, kraus + (int64_t)c * d2 * d2);
   __shared__ int s_r, s_bad;
   if (threadIdx.x == 0) {
     double emax = w[0] > 0 ? w[0] : 0, neg = 0;
@@ -54,7 +54,7 @@ __global__ void prune_and_build_kraus(int count, int nq, double tol, const doubl
   for (int e = threadIdx.x; e < d2 * d2; e += blockDim.x) {
     int i = e / d2, a = e % d2;
     cplx<double> v = mk<double>(0, 0);
-    if (i < s_r && !s_bad) v = sqrt(fmax(w[i], 0.0)) * vecs[(int64_t)c * d2 * d2 + a + (int64_t)i * d2];
+    if (i < s_r && !s_bad) v = sqrt(fmax(w[i], 0.0)) * GX(vecs, (int64_t)c * d2 * d2 + a + (int64_t)i * d2);
     K[e] = v;
   }
   __syncthreads();
@@ -70,7 +70,7 @@ __global__ void prune_and_build_kraus(int count, int nq, double tol, const doubl
         }
       if (!(err <= 1e-8)) s_bad = -2;
     }
-    ranks[c] = s_bad ? s_bad : s_r;
+    GX(ranks, c) = s_bad ? s_bad : s_r;
   }
   __syncthreads();
   if (s_bad)

@@ -1,7 +1,9 @@
 // Block-reflector helpers shared by the blocked Householder QR and the eigensolver's
 // back-transformation (256-thread CTAs).  A panel of pb <= NB Householder vectors sits in shared
 // memory (vector i at Vs + i * ldv); the product H_0 ... H_{pb-1} = I - V T V^H (compact WY form,
-// T upper triangular) is applied to a block of columns as two small matrix products.
+// T upper triangular) is applied to a block of columns as two small matrix products.  The block of
+// columns A is in global memory (its accesses are checked in the address-checked build); the panel,
+// T and the products are in shared memory.
 #pragma once
 #include "kernels.h"
 
@@ -33,8 +35,8 @@ __device__ void panel_vh_times(const cplx<R>* A, int64_t lda, int M, int nc, con
     const cplx<R>* a1p = a0p + lda;
 #pragma unroll 4
     for (int r = lane; r < M; r += 32) {
-      const cplx<R> a0 = a0p[r];
-      const cplx<R> a1 = two ? a1p[r] : mk<R>(0, 0);
+      const cplx<R> a0 = GX(a0p, r);
+      const cplx<R> a1 = two ? GX(a1p, r) : mk<R>(0, 0);
 #pragma unroll
       for (int i = 0; i < NB; ++i) {
         if (i < pb) {
@@ -81,8 +83,8 @@ __device__ void panel_minus_v_times(cplx<R>* A, int64_t lda, int M, int nc, cons
       for (int u = 0; u < RU; ++u) {
         const int r = r0 + 32 * u;
         if (r < M) {
-          x0[u] = a0p[r];
-          x1[u] = two ? a1p[r] : mk<R>(0, 0);
+          x0[u] = GX(a0p, r);
+          x1[u] = two ? GX(a1p, r) : mk<R>(0, 0);
         }
       }
 #pragma unroll
@@ -98,8 +100,8 @@ __device__ void panel_minus_v_times(cplx<R>* A, int64_t lda, int M, int nc, cons
             cfma(s1, v, y1[i]);
           }
         }
-        a0p[r] = x0[u] - s0;
-        if (two) a1p[r] = x1[u] - s1;
+        GX(a0p, r) = x0[u] - s0;
+        if (two) GX(a1p, r) = x1[u] - s1;
       }
     }
   }

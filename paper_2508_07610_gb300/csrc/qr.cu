@@ -58,18 +58,18 @@ __global__ void __launch_bounds__(NT) qr_kernel(QrArgs<R> g) {
 
   for (int64_t e = tid; e < (int64_t)m * n; e += NT) {
     int i = (int)(e % m), j = (int)(e / m);
-    cplx<R> v = in[view_row(g.vin, i) + view_col(g.vin, j)];
+    cplx<R> v = GX(in, view_row(g.vin, i) + view_col(g.vin, j));
     if (g.vin.conj) v.y = -v.y;
-    W[e] = v;
+    GX(W, e) = v;
   }
   __syncthreads();
 
   for (int j = 0; j < x; ++j) {
     cplx<R>* col = W + (int64_t)j * m;
     R s = 0;
-    for (int i = j + 1 + tid; i < m; i += NT) s += norm2(col[i]);
+    for (int i = j + 1 + tid; i < m; i += NT) s += norm2(GX(col, i));
     s = block_sum(s, red);
-    const cplx<R> a = col[j];
+    const cplx<R> a = GX(col, j);
     const R aa = sqrt(norm2(a));
     const R nrm = sqrt(aa * aa + s);
     cplx<R> ph = (aa > R(0)) ? mk<R>(a.x / aa, a.y / aa) : mk<R>(1, 0);
@@ -84,23 +84,23 @@ __global__ void __launch_bounds__(NT) qr_kernel(QrArgs<R> g) {
       for (int c = j + 1 + wid; c < n; c += NT / 32) {
         cplx<R>* y = W + (int64_t)c * m;
         cplx<R> acc = mk<R>(0, 0);
-        if (lane == 0) cfma_cj(acc, v0, y[j]);
-        for (int i = j + 1 + lane; i < m; i += 32) cfma_cj(acc, col[i], y[i]);
+        if (lane == 0) cfma_cj(acc, v0, GX(y, j));
+        for (int i = j + 1 + lane; i < m; i += 32) cfma_cj(acc, GX(col, i), GX(y, i));
         acc = warp_csum(acc);
         acc = beta * acc;
-        if (lane == 0) y[j] = y[j] - v0 * acc;
-        for (int i = j + 1 + lane; i < m; i += 32) y[i] = y[i] - col[i] * acc;
+        if (lane == 0) GX(y, j) = GX(y, j) - v0 * acc;
+        for (int i = j + 1 + lane; i < m; i += 32) GX(y, i) = GX(y, i) - GX(col, i) * acc;
       }
     }
     __syncthreads();
-    if (tid == 0) col[j] = (beta != R(0)) ? mk<R>(-nrm * ph.x, -nrm * ph.y) : a;
+    if (tid == 0) GX(col, j) = (beta != R(0)) ? mk<R>(-nrm * ph.x, -nrm * ph.y) : a;
     __syncthreads();
   }
 
   // Q = H_0 H_1 ... H_{x-1} [I; 0]: apply the reflectors to the identity columns, last first.
   for (int64_t e = tid; e < (int64_t)m * x; e += NT) {
     int i = (int)(e % m), c = (int)(e / m);
-    Q[e] = mk<R>(i == c ? R(1) : R(0), R(0));
+    GX(Q, e) = mk<R>(i == c ? R(1) : R(0), R(0));
   }
   __syncthreads();
   for (int j = x - 1; j >= 0; --j) {
@@ -111,27 +111,27 @@ __global__ void __launch_bounds__(NT) qr_kernel(QrArgs<R> g) {
     for (int c = j + wid; c < x; c += NT / 32) {
       cplx<R>* y = Q + (int64_t)c * m;
       cplx<R> acc = mk<R>(0, 0);
-      if (lane == 0) cfma_cj(acc, v0, y[j]);
-      for (int i = j + 1 + lane; i < m; i += 32) cfma_cj(acc, col[i], y[i]);
+      if (lane == 0) cfma_cj(acc, v0, GX(y, j));
+      for (int i = j + 1 + lane; i < m; i += 32) cfma_cj(acc, GX(col, i), GX(y, i));
       acc = warp_csum(acc);
       acc = beta * acc;
-      if (lane == 0) y[j] = y[j] - v0 * acc;
-      for (int i = j + 1 + lane; i < m; i += 32) y[i] = y[i] - col[i] * acc;
+      if (lane == 0) GX(y, j) = GX(y, j) - v0 * acc;
+      for (int i = j + 1 + lane; i < m; i += 32) GX(y, i) = GX(y, i) - GX(col, i) * acc;
     }
     __syncthreads();
   }
   // R: clear the reflectors below the diagonal of the leading x rows.
   for (int64_t e = tid; e < (int64_t)x * x; e += NT) {
     int i = (int)(e % x), j = (int)(e / x);
-    if (i > j) W[(int64_t)j * m + i] = mk<R>(0, 0);
+    if (i > j) GX(W, (int64_t)j * m + i) = mk<R>(0, 0);
   }
   if (g.qout) {
     cplx<R>* out = g.qout + view_batch(g.vq, z);
     for (int64_t e = tid; e < (int64_t)m * x; e += NT) {
       int i = (int)(e % m), c = (int)(e / m);
-      cplx<R> v = Q[e];
+      cplx<R> v = GX(Q, e);
       if (g.vq.conj) v.y = -v.y;
-      out[view_row(g.vq, i) + view_col(g.vq, c)] = v;
+      GX(out, view_row(g.vq, i) + view_col(g.vq, c)) = v;
     }
   }
 }
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(NT) qr_cluster_kernel(QrArgs<R> g, int C, int 
     int i = r0 + il;
     cplx<R> v = mk<R>(0, 0);
     if (i < r1) {
-      v = in[view_row(g.vin, i) + view_col(g.vin, j)];
+      v = GX(in, view_row(g.vin, i) + view_col(g.vin, j));
       if (g.vin.conj) v.y = -v.y;
     }
     Wl[e] = v;
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(NT) qr_cluster_kernel(QrArgs<R> g, int C, int 
   for (int64_t e = tid; e < (int64_t)mloc * n; e += NT) {
     int il = (int)(e % mloc), c = (int)(e / mloc);
     int i = r0 + il;
-    if (i < r1 && i < x) W[(int64_t)c * m + i] = (c >= i) ? Wl[e] : mk<R>(0, 0);
+    if (i < r1 && i < x) GX(W, (int64_t)c * m + i) = (c >= i) ? Wl[e] : mk<R>(0, 0);
   }
   __syncthreads();
   // Q in place: clear the strict upper triangle of the leading x columns, then apply the reflectors
@@ -314,10 +314,10 @@ __global__ void __launch_bounds__(NT) qr_cluster_kernel(QrArgs<R> g, int C, int 
     int i = r0 + il;
     if (i >= r1) continue;
     cplx<R> v = Wl[e];
-    Qg[(int64_t)c * m + i] = v;
+    GX(Qg, (int64_t)c * m + i) = v;
     if (out) {
       if (g.vq.conj) v.y = -v.y;
-      out[view_row(g.vq, i) + view_col(g.vq, c)] = v;
+      GX(out, view_row(g.vq, i) + view_col(g.vq, c)) = v;
     }
   }
   cluster.sync();  // no CTA leaves while a peer may still read its shared memory
@@ -358,9 +358,9 @@ __global__ void __launch_bounds__(NT) qr_blocked_kernel(QrArgs<R> g) {
 
   for (int64_t e = tid; e < (int64_t)m * n; e += NT) {
     int i = (int)(e % m), j = (int)(e / m);
-    cplx<R> v = in[view_row(g.vin, i) + view_col(g.vin, j)];
+    cplx<R> v = GX(in, view_row(g.vin, i) + view_col(g.vin, j));
     if (g.vin.conj) v.y = -v.y;
-    W[e] = v;
+    GX(W, e) = v;
   }
   __syncthreads();
 
@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(NT) qr_blocked_kernel(QrArgs<R> g) {
     const int p0 = P * NB, pb = (x - p0 < NB) ? x - p0 : NB, M = m - p0;
     for (int e = tid; e < pb * M; e += NT) {
       int i = e / M, r = e % M;
-      Vs[i * m + r] = W[(int64_t)(p0 + i) * m + p0 + r];
+      Vs[i * m + r] = GX(W, (int64_t)(p0 + i) * m + p0 + r);
     }
     __syncthreads();
     // factor the panel in shared memory
@@ -401,14 +401,14 @@ __global__ void __launch_bounds__(NT) qr_blocked_kernel(QrArgs<R> g) {
       cplx<R>* wc = W + (int64_t)(p0 + jj) * m + p0;
       for (int r = tid; r < M; r += NT) {
         if (r < jj) {
-          wc[r] = col[r];
+          GX(wc, r) = col[r];
           col[r] = mk<R>(0, 0);
         } else if (r > jj) {
-          wc[r] = col[r];
+          GX(wc, r) = col[r];
         }
       }
       if (tid == 0) {
-        wc[jj] = (beta != R(0)) ? mk<R>(-nrm * ph.x, -nrm * ph.y) : a;
+        GX(wc, jj) = (beta != R(0)) ? mk<R>(-nrm * ph.x, -nrm * ph.y) : a;
         col[jj] = v0;
         s_beta[p0 + jj] = beta;
         s_v0[p0 + jj] = v0;
@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(NT) qr_blocked_kernel(QrArgs<R> g) {
   // Q = H_0 H_1 ... H_{x-1} [I; 0], one block reflector I - V T V^H per panel, last panel first
   for (int64_t e = tid; e < (int64_t)m * x; e += NT) {
     int i = (int)(e % m), c = (int)(e / m);
-    Q[e] = mk<R>(i == c ? R(1) : R(0), R(0));
+    GX(Q, e) = mk<R>(i == c ? R(1) : R(0), R(0));
   }
   __syncthreads();
   for (int P = npan - 1; P >= 0; --P) {
@@ -467,7 +467,7 @@ __global__ void __launch_bounds__(NT) qr_blocked_kernel(QrArgs<R> g) {
       int i = e / M, r = e % M;
       cplx<R> v = mk<R>(0, 0);
       if (r == i) v = s_v0[p0 + i];
-      else if (r > i) v = W[(int64_t)(p0 + i) * m + p0 + r];
+      else if (r > i) v = GX(W, (int64_t)(p0 + i) * m + p0 + r);
       Vs[i * m + r] = v;
     }
     __syncthreads();
@@ -483,15 +483,15 @@ __global__ void __launch_bounds__(NT) qr_blocked_kernel(QrArgs<R> g) {
   // R: clear the reflectors below the diagonal of the leading x rows.
   for (int64_t e = tid; e < (int64_t)x * x; e += NT) {
     int i = (int)(e % x), j = (int)(e / x);
-    if (i > j) W[(int64_t)j * m + i] = mk<R>(0, 0);
+    if (i > j) GX(W, (int64_t)j * m + i) = mk<R>(0, 0);
   }
   if (g.qout) {
     cplx<R>* out = g.qout + view_batch(g.vq, z);
     for (int64_t e = tid; e < (int64_t)m * x; e += NT) {
       int i = (int)(e % m), c = (int)(e / m);
-      cplx<R> v = Q[e];
+      cplx<R> v = GX(Q, e);
       if (g.vq.conj) v.y = -v.y;
-      out[view_row(g.vq, i) + view_col(g.vq, c)] = v;
+      GX(out, view_row(g.vq, i) + view_col(g.vq, c)) = v;
     }
   }
 }

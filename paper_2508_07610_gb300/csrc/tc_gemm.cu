@@ -159,17 +159,17 @@ __global__ void tc_split_kernel(int rows, int K, int rows_per_tile, int RT, int 
     }
     cplx<float> x = mk<float>(0.f, 0.f);
     if (r < rows && k < K) {
-      x = transpose ? S[view_row(v, k) + view_col(v, r)] : S[view_row(v, r) + view_col(v, k)];
+      x = transpose ? GX(S, view_row(v, k) + view_col(v, r)) : GX(S, view_row(v, r) + view_col(v, k));
       if (v.conj) x.y = -x.y;
     }
     const float rh = tf32_rna(x.x), ih = tf32_rna(x.y);
     const int rt = r / rows_per_tile, rr = r % rows_per_tile, ks = k / TK, kk = k % TK;
     float* T = dst + per_z * z + ((int64_t)rt * KS + ks) * 4 * plane;
     const int o = core_off(rr, kk) / 4;
-    T[o] = rh;
-    T[plane + o] = tf32_rna(x.x - rh);
-    T[2 * plane + o] = ih;
-    T[3 * plane + o] = tf32_rna(x.y - ih);
+    GX(T, o) = rh;
+    GX(T, plane + o) = tf32_rna(x.x - rh);
+    GX(T, 2 * plane + o) = ih;
+    GX(T, 3 * plane + o) = tf32_rna(x.y - ih);
   }
 }
 
@@ -241,8 +241,8 @@ __global__ void __launch_bounds__(NTH, 1) tc_cgemm_kernel(TcParams p) {
         const uint32_t fb = smem_addr(&full[s]);
         const uint32_t dst = smem_addr(smem + s * STAGE_BYTES);
         mbar_expect_tx(fb, STAGE_BYTES);
-        bulk_g2s(dst, Abase + (int64_t)ks * A_STAGE, A_STAGE, fb);
-        bulk_g2s(dst + A_STAGE, Bbase + (int64_t)ks * B_STAGE, B_STAGE, fb);
+        bulk_g2s(dst, GRANGE(Abase + (int64_t)ks * A_STAGE, A_STAGE), A_STAGE, fb);
+        bulk_g2s(dst + A_STAGE, GRANGE(Bbase + (int64_t)ks * B_STAGE, B_STAGE), B_STAGE, fb);
         issued = ks + 1;
       }
       // every copy in flight has landed before the shared memory is given up (each stage's last phase)
@@ -341,16 +341,16 @@ __global__ void __launch_bounds__(NTH, 1) tc_cgemm_kernel(TcParams p) {
         const int64_t o = ro + view_col(p.vc, j);
         cplx<float> v = p.alpha * mk<float>(sre[c] + cre[c], sim[c] + cim[c]);
         if (use_beta) {
-          cplx<float> old = C[o];
+          cplx<float> old = GX(C, o);
           if (p.vc.conj) old.y = -old.y;
           v = v + p.beta * old;
         }
         if (p.vc.conj) v.y = -v.y;
-        C[o] = v;
+        GX(C, o) = v;
       }
     }
   }
-  if (tid == 0 && !ok && p.status) atomicOr(p.status, kStatusTimeout);
+  if (tid == 0 && !ok && p.status) atomicOr(GP(p.status), kStatusTimeout);
   if (warp == 1) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
@@ -416,7 +416,7 @@ __global__ void wait_timeout_probe(uint64_t limit_ns, int* status) {
   const uint32_t a = smem_addr(&bar);
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(a) : "memory");
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  if (!mbar_wait_bounded(a, 0, limit_ns)) atomicOr(status, kStatusTimeout);
+  if (!mbar_wait_bounded(a, 0, limit_ns)) atomicOr(GP(status), kStatusTimeout);
 }
 }  // namespace
 }  // namespace mpdo

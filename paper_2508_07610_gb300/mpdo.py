@@ -12,13 +12,15 @@ from typing import Optional, Sequence
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libmpdo.so")
+# MPDO_LIBRARY=bounds loads the address-checked debug build (build.build(bounds=True)) instead
+LIB_PATH = os.path.join(HERE, "libmpdo_bounds.so" if os.environ.get("MPDO_LIBRARY") == "bounds" else "libmpdo.so")
 
 FP64, MIXED, FP32 = 0, 1, 2
 PREC = {"fp64": FP64, "mixed": MIXED, "fp32": FP32}
 TRACE, ZZ, ZZ_MAP, GHZ, MAXCUT, PURITY, DISCARDED, DIMS, PROB = range(9)
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "not completely positive",
-          4: "not trace preserving", 5: "non-finite result", 6: "timeout", 7: "CUDA error", 8: "invalid state"}
+          4: "not trace preserving", 5: "non-finite result", 6: "timeout", 7: "CUDA error", 8: "invalid state",
+          9: "trace guard: Tr rho grew or became non-finite"}
 
 
 class MPDOError(RuntimeError):
@@ -36,7 +38,8 @@ def lib():
     if _lib is not None:
         return _lib
     if not os.path.exists(LIB_PATH):
-        raise ImportError(f"{LIB_PATH} is missing: build it with paper_2508_07610_gb300.build.build()")
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_2508_07610_gb300.build.build()"
+                          + ("  (bounds=True)" if LIB_PATH.endswith("_bounds.so") else ""))
     L = C.CDLL(LIB_PATH)
     vp, ip, dp, i32 = C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_int
     sig = {
@@ -69,6 +72,7 @@ def lib():
         "mpdo_set_centre": [vp, i32],
         "mpdo_profile": [vp, i32],
         "mpdo_set_neighbour_truncation": [vp, i32],
+        "mpdo_set_trace_guard": [vp, C.c_double],
         "mpdo_set_tensor_cores": [vp, i32],
         "mpdo_set_purity_memory": [vp, C.c_longlong],
         "mpdo_profile_read": [vp, dp, dp, C.POINTER(C.c_longlong)],
@@ -78,6 +82,10 @@ def lib():
         "mpdo_fidelity": [vp, i32, vp, i32, dp],
         "mpdo_distribution": [vp, dp],
         "mpdo_jsd": [dp, dp, i32, dp],
+        "mpdo_bounds_register": [vp, C.c_size_t],
+        "mpdo_bounds_unregister": [vp],
+        "mpdo_bounds_read": [C.POINTER(C.c_ulonglong), C.c_char_p, i32, ip, C.POINTER(C.c_ulonglong),
+                             C.POINTER(C.c_ulonglong)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -87,8 +95,35 @@ def lib():
     L.mpdo_launch_count.restype = C.c_longlong
     L.mpdo_status_string.argtypes = [C.c_int]
     L.mpdo_status_string.restype = C.c_char_p
+    L.mpdo_bounds_enabled.argtypes = []
+    L.mpdo_bounds_enabled.restype = C.c_int
     _lib = L
     return L
+
+
+def bounds_enabled() -> bool:
+    """True when the loaded library is the address-checked debug build."""
+    return bool(lib().mpdo_bounds_enabled())
+
+
+def bounds_register(ptr: int, nbytes: int):
+    """Declare a caller-owned device buffer (e.g. a torch tensor passed as U_dev) to the address
+    checks of the debug build; a no-op in the release library."""
+    _check(lib().mpdo_bounds_register(C.c_void_p(ptr), nbytes), "mpdo_bounds_register")
+
+
+def bounds_unregister(ptr: int):
+    _check(lib().mpdo_bounds_unregister(C.c_void_p(ptr)), "mpdo_bounds_unregister")
+
+
+def bounds_read() -> dict:
+    """Failed address checks since the last read (the debug build only), and the first one's site."""
+    fails, line, addr, nb = C.c_ulonglong(), C.c_int(), C.c_ulonglong(), C.c_ulonglong()
+    buf = C.create_string_buffer(64)
+    _check(lib().mpdo_bounds_read(C.byref(fails), buf, 64, C.byref(line), C.byref(addr), C.byref(nb)),
+           "mpdo_bounds_read")
+    return {"failures": fails.value, "file": buf.value.decode(), "line": line.value, "address": addr.value,
+            "bytes": nb.value}
 
 
 def _check(status: int, where: str):
@@ -247,6 +282,11 @@ class MPDO:
     def set_neighbour_truncation(self, enable: bool):
         _check(lib().mpdo_set_neighbour_truncation(self.h, 1 if enable else 0), "mpdo_set_neighbour_truncation")
 
+    def set_trace_guard(self, tol: float):
+        """With tol > 0 every gate and truncation checks afterwards that no chain's Tr rho grew by more
+        than tol relative since the previous one (MPDOError status 9 otherwise); 0 switches it off."""
+        _check(lib().mpdo_set_trace_guard(self.h, float(tol)), "mpdo_set_trace_guard")
+
     def truncate_kraus(self, q: int, kappa: int = 0) -> np.ndarray:
         out = np.zeros(self.batch)
         _check(lib().truncate_kraus(self.h, q, kappa, out.ctypes.data_as(C.POINTER(C.c_double))), "truncate_kraus")
@@ -387,10 +427,13 @@ def wait_selftest(limit_us: int):
 
 
 def run_circuit(circuit, chi_max: int, kappa_max: int, prec="fp64", stream: int = 0,
-                trunc_order: str = "split_first") -> MPDO:
-    """Apply a workloads.Circuit on one chain; each channel is converted on the GPU once."""
+                trunc_order: str = "split_first", trace_guard: float = 0.0) -> MPDO:
+    """Apply a workloads.Circuit on one chain; each channel is converted on the GPU once.  With
+    trace_guard > 0 every op is followed by the trace guard (MPDO.set_trace_guard)."""
     st = MPDO(circuit.n, chi_max, kappa_max, prec, 1, stream)
     st.set_trunc_order(trunc_order)
+    if trace_guard > 0:
+        st.set_trace_guard(trace_guard)
     chans = {}
     for op in circuit.ops:
         if op.kind == 8:

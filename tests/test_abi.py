@@ -15,7 +15,7 @@ def _declared():
         if fn.endswith(".h"):
             src = open(os.path.join(ROOT, "include", fn)).read()
             src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-            names |= set(re.findall(r"^\s*(?:mpdo_status|surr_status|const char\s*\*|long long)\s+(\w+)\s*\(", src,
+            names |= set(re.findall(r"^\s*(?:mpdo_status|surr_status|const char\s*\*|long long|int)\s+(\w+)\s*\(", src,
                                     flags=re.M))
     return names
 
@@ -69,3 +69,22 @@ def test_headers_compile_and_link_as_plain_c(tmp_path):
                         "-L", os.path.dirname(path), "-lmpdo", "-Wl,-rpath," + os.path.dirname(path)],
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_checked_library_builds_with_the_same_entry_points():
+    """The address-checked debug build (-DMPDO_BOUNDS) compiles from the same sources and exports
+    every declared entry point; it reports itself as checked, the release library as not, and the
+    release stubs touch no device (they run here without a GPU)."""
+    names = _declared()
+    checked = ctypes.CDLL(B.build(bounds=True))
+    missing = [n for n in sorted(names) if not hasattr(checked, n)]
+    assert not missing, missing
+    assert checked.mpdo_bounds_enabled() == 1
+    release = ctypes.CDLL(B.build())
+    assert release.mpdo_bounds_enabled() == 0
+    fails, line = ctypes.c_ulonglong(7), ctypes.c_int(7)
+    buf = ctypes.create_string_buffer(8)
+    assert release.mpdo_bounds_read(ctypes.byref(fails), buf, 8, ctypes.byref(line), None, None) == 8  # ESTATE
+    assert fails.value == 0 and line.value == 0 and buf.value == b""
+    release.mpdo_bounds_register.argtypes = [ctypes.c_void_p, ctypes.c_size_t]
+    assert release.mpdo_bounds_register(16, 64) == 0

@@ -203,6 +203,7 @@ def test_batch_with_per_chain_gates_and_channels():
         chans = [W.kraus_to_chi(W.random_channel_kraus(kind, 3 if kind == 1 else 5, rng)) for _ in range(B)]
         cs = st.channels(kind, chans)
         U_dev = torch.tensor(np.stack(Us), dtype=torch.complex128, device="cuda")
+        G.bounds_register(U_dev.data_ptr(), U_dev.numel() * U_dev.element_size())  # no-op in release
         keep += [cs, U_dev]
         (st.apply_1q_batch if kind == 1 else st.apply_2q_batch)(q, U_dev.data_ptr(), cs)
         for b in range(B):
@@ -228,6 +229,8 @@ def test_batch_channel_index_array():
     U = W.random_unitary(4, rng)
     U_dev = torch.tensor(np.stack([U] * B), dtype=torch.complex128, device="cuda")
     idx_dev = torch.tensor(idx, dtype=torch.int32, device="cuda")
+    for t in (U_dev, idx_dev):
+        G.bounds_register(t.data_ptr(), t.numel() * t.element_size())  # no-op in the release library
     st.apply_2q_batch(0, U_dev.data_ptr(), cs, idx_dev.data_ptr())
     st.apply_2q_batch(1, U_dev.data_ptr(), cs, idx_dev.data_ptr())
     st.sync()
