@@ -354,3 +354,30 @@ def test_three_qubit_split_weights_match_state_error():
     # Eckart-Young on the first split: the kept weight is the top-chi Schmidt weight of the exact state
     ex = exact.dense()
     assert abs(st.trace() - exact.trace() * (1 - w1) * (1 - w2)) < 1e-12 * exact.trace()
+
+
+@pytest.mark.parametrize("order", ["split_first", "kraus_first"])
+def test_trace_never_grows_op_by_op(order):
+    """The premise of the library's trace guard: the channels are trace preserving and every
+    truncation (Kraus leg, bond split, three-site splits, the global bond sweep) only removes weight,
+    so Tr rho is non-increasing op by op, and it strictly drops at a cut that discards weight."""
+    rng = np.random.default_rng(404)
+    circ = W.random_circuit(6, 40, rng, rank1=3, rank2=6, p3q=0.2)
+    ops = list(circ.ops)
+    ops.insert(20, W.sweep_op(2))
+    kraus = [C.chi_to_kraus(chi, nq) for nq, chi in circ.chis]
+    st = M.MPDO(6, 4, 2, trunc_order=order)
+    prev, drops = st.trace(), 0
+    for op in ops:
+        before = st.discarded_chi + st.discarded_kappa
+        if op.kind == 8:
+            st.truncate_bonds(op.q)
+        else:
+            (st.apply_1q, st.apply_2q, st.apply_3q)[op.kind - 1](op.q, op.U, kraus[op.chan])
+        tr = st.trace()
+        assert tr <= prev * (1 + 1e-12), (op.kind, tr, prev)
+        if st.discarded_chi + st.discarded_kappa > before + 1e-9:
+            assert tr < prev
+            drops += 1
+        prev = tr
+    assert drops > 10
