@@ -50,7 +50,8 @@ def test_gpu_tests_run_clean_under_address_checks(checked_env):
     tail = r.stdout[-4000:] + "\n" + r.stderr[-2000:]
     print(tail)
     assert r.returncode == 0, tail
-    assert " passed" in r.stdout and " failed" not in r.stdout and " error" not in r.stdout
+    summary = [s for s in r.stdout.splitlines() if " passed" in s][-1]
+    assert "failed" not in summary and "error" not in summary, summary
 
 
 DETECT = r"""
